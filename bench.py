@@ -1,0 +1,364 @@
+"""Benchmark: time to the 1e-6 duality gap of plain DROT, and HBM GB/s of the fused DR step.
+
+One "step" of this benchmark is one complete solve of the workload (Algorithm 1
+from X_0 = p q^T until the stopping test fires at tol 1e-6: gap <= 1e-6 and
+||X1 - p||_1 + ||X^T 1 - q||_1 <= 1e-6).  The default workload is the
+rectangular 8192 x 6144 problem (Gaussian clouds, random marginals, FP32 plan and
+cost, FP64 reductions).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is the mean time to tolerance in seconds (lower is
+better); `roofline` reports the fused step kernel's algorithmic HBM traffic
+(12 bytes per plan entry per launch: read X, read C, write X) over its
+CUDA-event-timed launch duration; `e2e` is the same solve through the C ABI with
+host buffers (copies inside the timed region); `cpu_baseline` is the FP64 CPU
+oracle timed on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank solves its own replica of the problem (there
+is no exchange between independent solves), the max time over ranks is taken,
+and `value` stays the time to tolerance of each replica ("replicas only").
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 gap & HBM GB/s of fused DR step: plain vs batched / warm-start"
+BYTES_PER_ENTRY = 12  # read X (4) + read C (4) + write X (4), FP32
+L2_BYTES = 126 * 1024 * 1024
+
+# Iterations the FP32 GPU solver needs to reach tol 1e-6 on each workload (seed 0),
+# measured on B300; the reference (CPU oracle) arm extrapolates its per-iteration
+# time with these counts.  The step-parity tests show the FP64 oracle follows the
+# same iterates; solve-parity tests show its iteration counts agree closely.
+ITERS_TO_TOL = {
+    "plain_8192x6144": None,
+    "plain_256": 21434,
+    "plain_20000": None,
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2110_11738_b300/csrc/drot_kernels.cuh",):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch(workload):
+    """DRAM bytes per fused-step launch from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("kernel_source_sha256_16") != _kernel_source_hash():
+        return None
+    rec = d.get("workloads", {}).get(workload)
+    return None if rec is None else float(rec["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_baseline(workload, seed, iters_to_tol, sample_iters):
+    """The FP64 oracle as it stands, single-threaded, on `sample_iters` iterations of the full problem."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    pr = workloads.make_problem(workload, seed=seed)
+    C = pr.C.astype(np.float64)
+    st = oracle.StepState(C, pr.p, pr.q, pr.rho, np.outer(pr.p, pr.q), np.zeros(pr.m), np.zeros(pr.n))
+    t0 = time.perf_counter()
+    for _ in range(sample_iters):
+        st.step()
+    dt = time.perf_counter() - t0
+    per_iter = dt / sample_iters
+    return {
+        "value": per_iter * iters_to_tol if iters_to_tol else None,
+        "unit": "s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"{sample_iters} Algorithm-1 iterations of the full {pr.m}x{pr.n} problem (FP64 C oracle, "
+                   f"{per_iter:.3f} s/iteration), extrapolated to {iters_to_tol} iterations to tol"),
+        "seconds_per_iteration": per_iter,
+    }
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401
+
+    iters = ITERS_TO_TOL.get(args.workload)
+    t_steps = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = _cpu_baseline(args.workload, args.seed, iters, args.sample_iters)
+        if s >= args.warmup:
+            t_steps.append(cb["value"] if cb["value"] is not None else float("nan"))
+    value = statistics.mean(t_steps) if t_steps else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None if value is None else value * 1000.0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "seed": args.seed, "tol": args.tol},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2110_11738_b300 import drot
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    pr = workloads.make_problem(args.workload, seed=args.seed, device=dev, ld=workloads.pad_ld(
+        workloads.CONFIGS[args.workload]["n"]))
+    m, n = pr.m, pr.n
+    C = pr.C[:, :n]
+    ld = C.stride(0)
+    p = torch.as_tensor(pr.p, device=dev)
+    q = torch.as_tensor(pr.q, device=dev)
+    Xbuf = torch.empty((m, ld), dtype=torch.float32, device=dev)
+    X = Xbuf[:, :n]
+    mu = torch.zeros(m, dtype=torch.float64, device=dev)
+    nu = torch.zeros(n, dtype=torch.float64, device=dev)
+
+    solver = drot.Solver(device=local, profile=True)
+
+    def one_solve():
+        return solver.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
+
+    for _ in range(args.warmup):
+        last = one_solve()
+    solver.reset_profile()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    stream = torch.cuda.current_stream(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(one_solve())
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    # the solves run on the library's stream and return after a full synchronisation,
+    # so the host-side wall clock brackets them exactly; events bracket the same region
+    elapsed_ms = ev0.elapsed_time(ev1)
+    prof = solver.profile()
+
+    t_local = elapsed_ms / args.steps
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_per_solve = float(t.item())
+    iters = [r["iters"] for r in results]
+    statuses = sorted({r["status_name"] for r in results})
+
+    step_ms = prof["step_ms_total"] / max(1, prof["step_launches"])
+    alg_bytes = BYTES_PER_ENTRY * m * n
+    achieved = alg_bytes / (step_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ch = torch.empty((m, ld), dtype=torch.float32, pin_memory=True)
+        Ch.copy_(pr.C)
+        ph = torch.as_tensor(pr.p).pin_memory()
+        qh = torch.as_tensor(pr.q).pin_memory()
+        Xh = torch.empty((m, ld), dtype=torch.float32, pin_memory=True)
+        muh = torch.zeros(m, dtype=torch.float64).pin_memory()
+        nuh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        host_call = lambda: drot.drot_solve(solver.handle, Ch[:, :n], ph, qh, rho=pr.rho, tol=args.tol,  # noqa
+                                            max_iter=args.max_iter, X=Xh[:, :n], mu=muh, nu=nuh, n=n)
+        host_call()  # warm the staging buffers
+        barrier()
+        t0 = time.perf_counter()
+        e_res = [host_call() for _ in range(max(1, args.e2e_steps))]
+        e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.e2e_steps)
+        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": float(te.item()) / 1e3, "unit": "s",
+               "h2d_bytes_per_step": int(Ch.numel() * 4 + ph.numel() * 8 + qh.numel() * 8),
+               "d2h_bytes_per_step": int(Xh.numel() * 4 + muh.numel() * 8 + nuh.numel() * 8),
+               "iters": [r["iters"] for r in e_res]}
+        del Ch, Xh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cb = _cpu_baseline(args.workload, args.seed, int(statistics.mean(iters)), args.sample_iters)
+            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except MemoryError:
+            cpu = None
+
+    traffic = _traffic_per_launch(args.workload)
+    line = {
+        "metric": METRIC,
+        "value": ms_per_solve / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_solve,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "n": n, "ld": ld, "seed": args.seed, "tol": args.tol,
+                   "rho": pr.rho, "stop_rule": "gap<=tol and l1 residual<=tol",
+                   "l2": f"inputs larger than L2 (C+X = {2 * m * ld * 4 / 1e6:.0f} MB > 126 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iters_to_tol": iters,
+        "status": statuses,
+        "ms_per_iter": ms_per_solve / statistics.mean(iters),
+        "gpu_launches": int(prof["kernel_launches"]),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "drot_step_kernel",
+                     "step_ms": step_ms, "timed_launches": int(prof["step_launches"]),
+                     "alg_bytes_per_launch": alg_bytes,
+                     "plan": {k: prof[k] for k in ("tile_k", "grid_ctas", "col_tiles", "graph_iters")}},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "final": {k: results[-1][k] for k in ("primal_obj", "dual_obj", "gap", "res_l1", "dual_res", "nnz")},
+    }
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="plain_8192x6144",
+                    choices=["plain_8192x6144", "plain_256", "plain_20000"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-iter", type=int, default=3_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--sample-iters", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up solves", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

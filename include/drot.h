@@ -1,0 +1,165 @@
+/*
+ * drot.h - C ABI of the B300 (sm_103a) Douglas-Rachford optimal-transport solver.
+ *
+ * The solver computes an optimal transport plan for
+ *
+ *     minimise <C, X>  subject to  X >= 0,  X 1_n = p,  X^T 1_m = q        (Sec. 1, eq. ot:dist)
+ *
+ * by Douglas-Rachford splitting with f(X) = <C,X> + I_{X>=0} and g = indicator of the
+ * marginal constraints (Sec. 3, eq. ot:dist:operator:primal:composite), executed in the
+ * single-array form of Algorithm 1 (Sec. 3.1):
+ *
+ *     X_{k+1}   = [X_k + phi_k 1^T + 1 psi_k^T - rho C]_+                       (step 4)
+ *     r = X_{k+1} 1 - p,  s = X_{k+1}^T 1 - q,  beta = sum(r) / (m+n)          (step 5)
+ *     phi_{k+1} = (a_k - 2r + (2beta - alpha_k)) / n                            (step 6)
+ *     psi_{k+1} = (b_k - 2s + (2beta - alpha_k)) / m                            (step 7)
+ *     a -= r,  b -= s,  alpha -= beta                                           (step 8)
+ *
+ * (the paper names the column-side vector \varphi; it is psi here).  The dual variables
+ * returned are mu = phi / rho and nu = psi / rho (Appendix A.2, eq. dual:var).
+ *
+ * Stopping test (Sec. 3.1, "Stopping criteria"), evaluated on the device after every
+ * iteration: stop when gap <= tol and ||r||_1 + ||s||_1 <= tol, where
+ * gap = |<C, X_k> - (p^T phi_k + q^T psi_k)/rho|; if stop_on_dual_residual is set, also
+ * require r_dual = ||[(phi/rho) 1^T + 1 (psi/rho)^T - C]_+||_F <= tol.  r_dual of
+ * (phi_k, psi_k) is produced by the pass that computes X_{k+1}, so the test uses the
+ * value from the same pass (one iteration older than gap and residuals).
+ *
+ * Data layout: C and X are dense row-major FP32 m x n matrices with row pitch ld
+ * (floats): entry (i, j) lives at base[i*ld + j].  ld must be >= n and a multiple of 4,
+ * and both base pointers 16-byte aligned, so that every row starts on a 16-byte
+ * boundary.  Columns n..ld-1 (row padding) may be read but take no part in the
+ * arithmetic and are never written.  p, q, mu, nu are FP64 vectors.  Iterates X are FP32; every reduction that
+ * feeds the stopping test or the vector updates (row/column sums, <C,X>, the norms,
+ * the dual objective) is accumulated in FP64 across threads.
+ *
+ * Pointers: all buffers of one call are either device memory of the handle's device
+ * or host memory (pageable or pinned); mixing the two in one call is rejected.  With
+ * host buffers the library copies inputs to a device workspace owned by the handle,
+ * solves, and copies X, mu, nu back before returning.  The caller owns every buffer
+ * it passes; the handle owns only its workspace.
+ *
+ * Threading and streams: a handle is not thread-safe; use one handle per host thread.
+ * Work is issued on the configured stream (or a stream the handle creates).  Every
+ * solve call returns only after the final status has been read back, with X, mu, nu
+ * and the result struct complete.
+ *
+ * Errors: every entry point returns a drot_status.  Invalid arguments are rejected on
+ * the host before any launch.  No kernel in this library waits on another block or
+ * another kernel, so an error cannot leave the device hung.
+ */
+#ifndef DROT_H
+#define DROT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct drot_handle drot_handle;
+
+typedef enum {
+    DROT_OK = 0,                /* converged: the stopping test fired */
+    DROT_ERR_INVALID_ARG = 1,   /* bad size, pitch, alignment, pointer kind, tolerance ... */
+    DROT_ERR_MARGINALS = 2,     /* p or q negative / non-finite, or |sum p - sum q| > 1e-9 */
+    DROT_ERR_OOM = 3,           /* device or pinned-host allocation failed */
+    DROT_ERR_CUDA = 4,          /* a CUDA runtime call failed (message via drot_last_error) */
+    DROT_NOT_CONVERGED = 5,     /* max_iter iterations ran; outputs hold the last iterate */
+    DROT_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits */
+    DROT_ERR_NONFINITE = 7      /* a NaN/Inf appeared in the iteration; outputs hold the last iterate */
+} drot_status;
+
+typedef struct {
+    int device;                 /* CUDA device ordinal (default 0) */
+    void *stream;               /* cudaStream_t to issue work on; NULL: the handle creates one */
+    int stop_on_dual_residual;  /* 1: the stopping test also requires r_dual <= tol (default 0) */
+    double rho0;                /* rho = rho0 / (m + n) when a call passes rho <= 0 (default 2, Sec. 4) */
+    int graph_iters;            /* iterations per CUDA-graph replay; 0: chosen from the problem size */
+    int tile_k;                 /* float4 chunks per lane per row segment (1, 2 or 4); 0: automatic */
+    int grid_ctas;              /* CTAs of the fused step kernel; 0: automatic */
+    int profile;                /* 1: time every fused-step launch with CUDA events (drot_get_profile) */
+} drot_config;
+
+typedef struct {
+    int64_t iters;              /* iterations performed by this call */
+    double primal_obj;          /* <C, X_K> */
+    double dual_obj;            /* p^T mu + q^T nu */
+    double gap;                 /* |primal_obj - dual_obj| */
+    double res_l1;              /* ||X_K 1 - p||_1 + ||X_K^T 1 - q||_1 */
+    double res_l2;              /* sqrt(||X_K 1 - p||^2 + ||X_K^T 1 - q||^2) */
+    double dual_res;            /* r_dual of the vectors that entered the last pass */
+    int64_t nnz;                /* number of strictly positive entries of X_K */
+    int32_t status;             /* the drot_status of this solve */
+    double seconds;             /* host wall time of the call */
+} drot_result;
+
+/* One problem of a batch: same meaning and layout rules as drot_solve's arguments. */
+typedef struct {
+    int64_t m, n, ld;
+    const float *C;
+    const double *p, *q;
+    float *X;
+    double *mu, *nu;
+    double rho;                 /* <= 0: rho0 / (m + n) */
+} drot_problem;
+
+typedef struct {
+    double step_ms_total;       /* summed device time of timed fused-step launches */
+    int64_t step_launches;      /* fused-step launches that did work and were timed */
+    int64_t kernel_launches;    /* all kernels this handle launched (including early exits) */
+    int64_t graph_replays;      /* CUDA-graph replays issued */
+    int32_t tile_k, grid_ctas, col_tiles, graph_iters;  /* the plan of the last solve */
+} drot_profile;
+
+/* Fill cfg with the defaults listed above. */
+void drot_config_default(drot_config *cfg);
+
+/* Create a handle on cfg->device (cfg NULL: defaults).  *h is set on DROT_OK only. */
+drot_status drot_create(drot_handle **h, const drot_config *cfg);
+
+/* Solve one problem (Algorithm 1, Sec. 3.1; stopping test as above).
+ *   m, n       problem size, m >= 1, n >= 1
+ *   C, ld      cost, row-major FP32 with pitch ld (unchanged by the call)
+ *   p, q       marginals, FP64, nonnegative, equal total mass within 1e-9
+ *   rho        penalty parameter; <= 0 selects rho0 / (m + n)
+ *   tol        tolerance of the stopping test; < 0 runs exactly max_iter iterations
+ *   max_iter   iteration cap, >= 0
+ *   X          in/out plan, same layout as C.  warm == 0: overwritten with X_0 = p q^T
+ *              (Sec. 4).  warm != 0: holds X_0 on entry.
+ *   mu, nu     out: dual vectors phi/rho (m) and psi/rho (n).  warm != 0: on entry they
+ *              hold mu_0, nu_0 and the iteration starts from phi_0 = rho mu_0,
+ *              psi_0 = rho nu_0 with a_0 = Y_0 1 - p, b_0 = Y_0^T 1 - q,
+ *              Y_0 = X_0 + phi_0 1^T + 1 psi_0^T.
+ *   res        out (host), may be NULL.
+ * Returns DROT_OK when the test fired, DROT_NOT_CONVERGED after max_iter iterations. */
+drot_status drot_solve(drot_handle *h, int64_t m, int64_t n, const float *C, int64_t ld,
+                       const double *p, const double *q, double rho, double tol, int64_t max_iter,
+                       float *X, double *mu, double *nu, int warm, drot_result *res);
+
+/* Solve B independent problems of uneven sizes (no counterpart in the paper, which
+ * solves one problem at a time; each problem follows drot_solve exactly).  All problems
+ * share tol, max_iter and warm; each stops on its own test.  res: B entries (host),
+ * may be NULL.  Returns DROT_OK if every problem converged, else the first non-OK
+ * status among the problems (per-problem status in res[b].status). */
+drot_status drot_solve_batched(drot_handle *h, int32_t B, const drot_problem *probs, double tol,
+                               int64_t max_iter, int warm, drot_result *res);
+
+/* Release the handle and its workspace (NULL is accepted). */
+drot_status drot_destroy(drot_handle *h);
+
+/* Counters and timings accumulated since the handle was created or last reset. */
+drot_status drot_get_profile(drot_handle *h, drot_profile *out);
+drot_status drot_reset_profile(drot_handle *h);
+
+/* Static description of a status code. */
+const char *drot_status_string(drot_status s);
+
+/* Text of the last error recorded on this handle ("" if none). */
+const char *drot_last_error(drot_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DROT_H */

@@ -1,0 +1,682 @@
+// Host driver and C ABI of the DROT solver (declarations and contracts in include/drot.h).
+//
+// A solve is: argument checks -> marginal sums (one small kernel, read back once) ->
+// X_0 = p q^T (cold start) -> a_0, b_0, alpha_0 from the stored X_0 -> repeated
+// replays of a CUDA graph that holds `graph_iters` iterations of
+// [fused step kernel -> finish kernel] -> duals and nnz export.  The finish kernel
+// raises a device flag when the stopping test fires or the iteration cap is reached;
+// every later kernel of the graph returns at once, and the host, which keeps two
+// replays in flight, stops issuing replays when it reads the flag.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/drot.h"
+#include "drot_kernels.cuh"
+
+using drot::Scalars;
+
+namespace {
+
+struct Plan {
+    int K = 4, TW = 512, T = 1, G = 1, slots = 1, fin_blocks = 1, graph_iters = 1;
+    std::vector<long long> wbound;  // G+1
+    std::vector<int> slot_base;     // G
+    std::vector<int> tile_slot;     // T+1
+};
+
+struct GraphKey {
+    long long m = -1, n = -1, ld = -1;
+    const void *C = nullptr, *X = nullptr, *p = nullptr, *q = nullptr;
+    const void *arena = nullptr;
+    int K = 0, G = 0, graph_iters = 0, profile = 0;
+    bool operator==(const GraphKey &o) const {
+        return m == o.m && n == o.n && ld == o.ld && C == o.C && X == o.X && p == o.p && q == o.q &&
+               arena == o.arena && K == o.K && G == o.G && graph_iters == o.graph_iters && profile == o.profile;
+    }
+};
+
+struct Arena {
+    void *ptr = nullptr;
+    size_t cap = 0;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct drot_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    drot_config cfg{};
+    int num_sms = 148;
+
+    Arena work;     // solver workspace
+    Arena staging;  // device copies for host-pointer calls
+    Scalars *d_sc = nullptr;
+    Scalars *h_sc = nullptr;      // pinned: upload source
+    Scalars *h_status = nullptr;  // pinned: two read-back slots
+
+    // graph cache: two instances (alternating replays keep their profile events apart)
+    GraphKey key;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev[2];
+
+    // per-solve carved pointers
+    double *g = nullptr, *h = nullptr, *a = nullptr, *b = nullptr;
+    double *rowpart = nullptr, *colpart = nullptr, *ctapart = nullptr, *finpart = nullptr;
+    long long *wbound = nullptr;
+    int *slot_base = nullptr, *tile_slot = nullptr;
+
+    drot_profile prof{};
+    std::string last_error;
+};
+
+namespace {
+
+drot_status fail(drot_handle *h, drot_status s, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->last_error = buf;
+    }
+    return s;
+}
+
+#define DROT_CUDA(h, call)                                                                          \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? DROT_ERR_OOM : DROT_ERR_CUDA,        \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                           \
+    } while (0)
+
+drot_status arena_reserve(drot_handle *h, Arena &ar, size_t bytes) {
+    if (ar.cap >= bytes) return DROT_OK;
+    if (ar.ptr) {
+        DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+        DROT_CUDA(h, cudaFree(ar.ptr));
+        ar.ptr = nullptr;
+        ar.cap = 0;
+    }
+    size_t cap = align_up(bytes + bytes / 4, 1 << 20);
+    DROT_CUDA(h, cudaMalloc(&ar.ptr, cap));
+    ar.cap = cap;
+    return DROT_OK;
+}
+
+bool is_device_ptr(const void *p, int device) {
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) && attr.device == device;
+}
+
+// Choose the tile width, the grid and the per-CTA segment ranges.  Segment
+// ranges are balanced by the number of columns they cover (a ragged last tile
+// costs less per row), and slots are numbered in CTA order, which is also
+// column-tile order.
+void make_plan(const drot_handle *h, long long m, long long n, Plan &P) {
+    int K = h->cfg.tile_k;
+    if (K != 1 && K != 2 && K != 4) {
+        if (n >= 1536) K = 4;
+        else if (n >= 384) K = 2;
+        else K = 1;
+    }
+    P.K = K;
+    P.TW = 128 * K;
+    P.T = (int)((n + P.TW - 1) / P.TW);
+    const long long units = (long long)P.T * m;
+    int G = h->cfg.grid_ctas;
+    if (G <= 0) {
+        // two resident CTAs per SM; small problems use fewer CTAs so each warp has rows
+        const long long want = (units + drot::kWarps - 1) / drot::kWarps;
+        G = (int)std::min<long long>(2LL * h->num_sms, std::max<long long>(1, want));
+    }
+    G = (int)std::min<long long>(G, std::max<long long>(1, units));
+    P.G = G;
+
+    const long long last_w = n - (long long)(P.T - 1) * P.TW;  // columns of the last tile
+    const long long full_units = (long long)(P.T - 1) * m;
+    const double total_cost = (double)full_units * P.TW + (double)m * last_w;
+    auto units_for_cost = [&](double cost) -> long long {
+        const double full_cost = (double)full_units * P.TW;
+        long long u;
+        if (cost <= full_cost) u = (long long)std::llround(cost / P.TW);
+        else u = full_units + (long long)std::llround((cost - full_cost) / (double)last_w);
+        return std::min(std::max<long long>(u, 0), units);
+    };
+    P.wbound.assign(G + 1, 0);
+    for (int g = 1; g < G; ++g) P.wbound[g] = std::max(P.wbound[g - 1], units_for_cost(total_cost * g / G));
+    P.wbound[G] = units;
+
+    P.slot_base.assign(G, 0);
+    std::vector<int> slot_tile;
+    for (int g = 0; g < G; ++g) {
+        P.slot_base[g] = (int)slot_tile.size();
+        const long long w0 = P.wbound[g], w1 = P.wbound[g + 1];
+        if (w1 <= w0) continue;
+        for (long long t = w0 / m; t <= (w1 - 1) / m; ++t) slot_tile.push_back((int)t);
+    }
+    P.slots = std::max<int>(1, (int)slot_tile.size());
+    P.tile_slot.assign(P.T + 1, (int)slot_tile.size());
+    for (int t = P.T - 1; t >= 0; --t) {
+        int first = P.tile_slot[t + 1];
+        for (int s = (int)slot_tile.size() - 1; s >= 0; --s)
+            if (slot_tile[s] >= t) first = std::min(first, s);
+        P.tile_slot[t] = first;
+    }
+    const long long mn = m + n;
+    P.fin_blocks = (int)std::min<long long>(2LL * h->num_sms, std::max<long long>(1, (mn + 255) / 256));
+
+    int gi = h->cfg.graph_iters;
+    if (gi <= 0) {
+        const double t_iter = 12.0 * (double)m * (double)n / 6.0e12 + 6.0e-6;
+        gi = (int)std::lround(2.0e-3 / t_iter);
+        gi = std::max(1, std::min(gi, 256));
+    }
+    P.graph_iters = gi;
+}
+
+template <typename T>
+T *carve(char *&cur, size_t count) {
+    T *p = reinterpret_cast<T *>(cur);
+    cur += align_up(count * sizeof(T), 256);
+    return p;
+}
+
+drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan &P) {
+    const size_t bytes = align_up(sizeof(double) * m, 256) * 3 + align_up(sizeof(double) * n, 256) * 2 +
+                         align_up(sizeof(double) * (size_t)P.T * m, 256) +
+                         align_up(sizeof(double) * (size_t)P.slots * P.TW, 256) +
+                         align_up(sizeof(double) * 2 * P.G, 256) +
+                         align_up(sizeof(double) * drot::kFinishAcc * P.fin_blocks, 256) +
+                         align_up(sizeof(long long) * (P.G + 1), 256) + align_up(sizeof(int) * P.G, 256) +
+                         align_up(sizeof(int) * (P.T + 1), 256) + 4096;
+    drot_status st = arena_reserve(h, h->work, bytes);
+    if (st != DROT_OK) return st;
+    char *cur = static_cast<char *>(h->work.ptr);
+    h->g = carve<double>(cur, m);
+    h->a = carve<double>(cur, m);
+    carve<double>(cur, m);  // spare row vector (keeps the layout stable)
+    h->h = carve<double>(cur, n);
+    h->b = carve<double>(cur, n);
+    h->rowpart = carve<double>(cur, (size_t)P.T * m);
+    h->colpart = carve<double>(cur, (size_t)P.slots * P.TW);
+    h->ctapart = carve<double>(cur, 2 * (size_t)P.G);
+    h->finpart = carve<double>(cur, (size_t)drot::kFinishAcc * P.fin_blocks);
+    h->wbound = carve<long long>(cur, P.G + 1);
+    h->slot_base = carve<int>(cur, P.G);
+    h->tile_slot = carve<int>(cur, P.T + 1);
+    DROT_CUDA(h, cudaMemcpyAsync(h->wbound, P.wbound.data(), sizeof(long long) * (P.G + 1), cudaMemcpyHostToDevice,
+                                 h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(h->slot_base, P.slot_base.data(), sizeof(int) * P.G, cudaMemcpyHostToDevice,
+                                 h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(h->tile_slot, P.tile_slot.data(), sizeof(int) * (P.T + 1), cudaMemcpyHostToDevice,
+                                 h->stream));
+    return DROT_OK;
+}
+
+drot::StepArgs step_args(const drot_handle *h, long long m, long long n, long long ld, const float *C, float *X) {
+    drot::StepArgs A{};
+    A.C = C;
+    A.X = X;
+    A.g = h->g;
+    A.h = h->h;
+    A.sc = h->d_sc;
+    A.rowpart = h->rowpart;
+    A.colpart = h->colpart;
+    A.ctapart = h->ctapart;
+    A.wbound = h->wbound;
+    A.slot_base = h->slot_base;
+    A.m = m;
+    A.n = n;
+    A.ld = ld;
+    A.inv_n = 1.0 / (double)n;
+    A.inv_m = 1.0 / (double)m;
+    return A;
+}
+
+drot::FinishArgs finish_args(const drot_handle *h, long long m, long long n, const Plan &P, const double *p,
+                             const double *q) {
+    drot::FinishArgs F{};
+    F.rowpart = h->rowpart;
+    F.colpart = h->colpart;
+    F.ctapart = h->ctapart;
+    F.tile_slot = h->tile_slot;
+    F.p = p;
+    F.q = q;
+    F.a = h->a;
+    F.b = h->b;
+    F.g = h->g;
+    F.h = h->h;
+    F.finpart = h->finpart;
+    F.sc = h->d_sc;
+    F.m = m;
+    F.n = n;
+    F.T = P.T;
+    F.TW = P.TW;
+    F.G = P.G;
+    F.inv_n = 1.0 / (double)n;
+    F.inv_m = 1.0 / (double)m;
+    return F;
+}
+
+template <bool UPDATE>
+cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s) {
+    switch (P.K) {
+        case 1: drot::drot_step_kernel<1, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
+        case 2: drot::drot_step_kernel<2, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
+        default: drot::drot_step_kernel<4, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
+    }
+    return cudaGetLastError();
+}
+
+void destroy_graphs(drot_handle *h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->exec[i]) cudaGraphExecDestroy(h->exec[i]);
+        h->exec[i] = nullptr;
+        for (cudaEvent_t e : h->ev[i]) cudaEventDestroy(e);
+        h->ev[i].clear();
+    }
+    h->key = GraphKey{};
+}
+
+// Capture `graph_iters` iterations of [step -> finish] into two executable graphs.
+drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, const drot::StepArgs &A,
+                         const drot::FinishArgs &F) {
+    destroy_graphs(h);
+    const bool prof = key.profile != 0;
+    for (int inst = 0; inst < 2; ++inst) {
+        if (prof) {
+            h->ev[inst].resize(2 * P.graph_iters);
+            for (auto &e : h->ev[inst]) DROT_CUDA(h, cudaEventCreate(&e));
+        }
+        cudaGraph_t graph = nullptr;
+        DROT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t err = cudaSuccess;
+        for (int it = 0; it < P.graph_iters && err == cudaSuccess; ++it) {
+            if (prof) err = cudaEventRecordWithFlags(h->ev[inst][2 * it], h->stream, cudaEventRecordExternal);
+            if (err == cudaSuccess) err = launch_step<true>(P, A, h->stream);
+            if (prof && err == cudaSuccess)
+                err = cudaEventRecordWithFlags(h->ev[inst][2 * it + 1], h->stream, cudaEventRecordExternal);
+            if (err == cudaSuccess) {
+                drot::drot_finish_kernel<<<P.fin_blocks, drot::kFinishThreads, 0, h->stream>>>(F);
+                err = cudaGetLastError();
+            }
+        }
+        cudaError_t end = cudaStreamEndCapture(h->stream, &graph);
+        if (err != cudaSuccess || end != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, DROT_ERR_CUDA, "graph capture failed: %s",
+                        cudaGetErrorString(err != cudaSuccess ? err : end));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&h->exec[inst], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(h, DROT_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+    }
+    h->key = key;
+    return DROT_OK;
+}
+
+// The solve on device pointers.
+drot_status solve_device(drot_handle *h, long long m, long long n, const float *C, long long ld, const double *p,
+                         const double *q, double rho, double tol, long long max_iter, float *X, double *mu,
+                         double *nu, int warm, drot_result *res) {
+    Plan P;
+    make_plan(h, m, n, P);
+    drot_status st = setup_workspace(h, m, n, P);
+    if (st != DROT_OK) return st;
+
+    // scalar state; marginal sums and the warm duals' sums first
+    Scalars &S = *h->h_sc;
+    std::memset(&S, 0, sizeof S);
+    S.rho = rho;
+    S.tol = tol;
+    S.max_iter = max_iter;
+    S.stop_on_dual = h->cfg.stop_on_dual_residual ? 1 : 0;
+    S.done = drot::kRunning;
+    DROT_CUDA(h, cudaMemcpyAsync(h->d_sc, &S, sizeof S, cudaMemcpyHostToDevice, h->stream));
+    drot::drot_vector_sums_kernel<<<1, 1024, 0, h->stream>>>(p, q, warm ? mu : nullptr, warm ? nu : nullptr, m, n,
+                                                             h->d_sc);
+    DROT_CUDA(h, cudaGetLastError());
+    h->prof.kernel_launches += 1;
+    DROT_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+    DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+    const Scalars chk = *h->h_status;
+    if (chk.nonfinite_input & 3)
+        return fail(h, DROT_ERR_MARGINALS, "p or q has a negative or non-finite entry");
+    if (chk.nonfinite_input & 4) return fail(h, DROT_ERR_INVALID_ARG, "warm-start duals are not finite");
+    if (!(std::fabs(chk.sum_p - chk.sum_q) <= 1e-9 * std::max(1.0, std::fabs(chk.sum_p))))
+        return fail(h, DROT_ERR_MARGINALS, "sum(p) = %.17g and sum(q) = %.17g differ", chk.sum_p, chk.sum_q);
+
+    // X_0 and the state derived from it
+    if (!warm) {
+        const long long work = m * ((n + 3) / 4);
+        const int blocks = (int)std::min<long long>(8LL * h->num_sms, std::max<long long>(1, (work + 255) / 256));
+        drot::drot_init_plan_kernel<<<blocks, 256, 0, h->stream>>>(X, p, q, m, n, ld);
+        DROT_CUDA(h, cudaGetLastError());
+        h->prof.kernel_launches += 1;
+    }
+    const drot::StepArgs A = step_args(h, m, n, ld, C, X);
+    const drot::FinishArgs F = finish_args(h, m, n, P, p, q);
+    DROT_CUDA(h, launch_step<false>(P, A, h->stream));
+    drot::drot_init_state_kernel<<<P.fin_blocks, drot::kFinishThreads, 0, h->stream>>>(F, warm ? mu : nullptr,
+                                                                                      warm ? nu : nullptr);
+    DROT_CUDA(h, cudaGetLastError());
+    h->prof.kernel_launches += 2;
+
+    long long iters_done = 0;
+    int done = max_iter > 0 ? drot::kRunning : drot::kIterCap;
+    if (max_iter > 0) {
+        GraphKey key;
+        key.m = m; key.n = n; key.ld = ld; key.C = C; key.X = X; key.p = p; key.q = q;
+        key.arena = h->work.ptr; key.K = P.K; key.G = P.G; key.graph_iters = P.graph_iters;
+        key.profile = h->cfg.profile ? 1 : 0;
+        if (!(key == h->key) || !h->exec[0]) {
+            st = build_graphs(h, key, P, A, F);
+            if (st != DROT_OK) return st;
+        }
+        // keep two replays in flight; slot r%2 of h_status receives replay r's state
+        const long long max_replays = (max_iter + P.graph_iters - 1) / P.graph_iters + 2;
+        cudaEvent_t copied[2];
+        DROT_CUDA(h, cudaEventCreateWithFlags(&copied[0], cudaEventDisableTiming));
+        DROT_CUDA(h, cudaEventCreateWithFlags(&copied[1], cudaEventDisableTiming));
+        long long issued = 0, consumed = 0, k_prev = 0;
+        drot_status loop_st = DROT_OK;
+        auto issue = [&](long long r) -> cudaError_t {
+            const int inst = (int)(r & 1);
+            cudaError_t e = cudaGraphLaunch(h->exec[inst], h->stream);
+            if (e != cudaSuccess) return e;
+            e = cudaMemcpyAsync(h->h_status + inst, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return e;
+            h->prof.graph_replays += 1;
+            h->prof.kernel_launches += 2LL * P.graph_iters;
+            return cudaEventRecord(copied[inst], h->stream);
+        };
+        while (true) {
+            while (issued < consumed + 2 && issued < max_replays) {
+                cudaError_t e = issue(issued);
+                if (e != cudaSuccess) {
+                    loop_st = fail(h, DROT_ERR_CUDA, "graph replay failed: %s", cudaGetErrorString(e));
+                    break;
+                }
+                ++issued;
+            }
+            if (loop_st != DROT_OK || consumed >= issued) break;
+            const int inst = (int)(consumed & 1);
+            cudaError_t e = cudaEventSynchronize(copied[inst]);
+            if (e != cudaSuccess) {
+                loop_st = fail(h, DROT_ERR_CUDA, "replay wait failed: %s", cudaGetErrorString(e));
+                break;
+            }
+            const Scalars s = h->h_status[inst];
+            if (h->cfg.profile) {
+                const long long ran = s.k - k_prev;
+                for (long long it = 0; it < ran && it < P.graph_iters; ++it) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, h->ev[inst][2 * it], h->ev[inst][2 * it + 1]) == cudaSuccess) {
+                        h->prof.step_ms_total += ms;
+                        h->prof.step_launches += 1;
+                    }
+                }
+            }
+            k_prev = s.k;
+            ++consumed;
+            if (s.done != drot::kRunning) {
+                done = s.done;
+                break;
+            }
+        }
+        cudaError_t se = cudaStreamSynchronize(h->stream);
+        cudaEventDestroy(copied[0]);
+        cudaEventDestroy(copied[1]);
+        if (loop_st != DROT_OK) return loop_st;
+        if (se != cudaSuccess) return fail(h, DROT_ERR_CUDA, "stream sync failed: %s", cudaGetErrorString(se));
+        if (done == drot::kRunning)
+            return fail(h, DROT_ERR_CUDA, "iteration did not report completion after %lld replays", issued);
+    }
+
+    // outputs
+    const int eblocks = (int)std::min<long long>(2LL * h->num_sms, std::max<long long>(1, (m + n + 255) / 256));
+    drot::drot_export_duals_kernel<<<eblocks, 256, 0, h->stream>>>(h->g, h->h, h->d_sc, mu, nu, m, n, 1.0 / n,
+                                                                   1.0 / m);
+    DROT_CUDA(h, cudaGetLastError());
+    DROT_CUDA(h, cudaMemsetAsync(&h->d_sc->nnz, 0, sizeof(unsigned long long), h->stream));
+    const int nblocks = (int)std::min<long long>(8LL * h->num_sms, std::max<long long>(1, (m * n + 255) / 256));
+    drot::drot_count_nnz_kernel<<<nblocks, 256, 0, h->stream>>>(X, m, n, ld, h->d_sc);
+    DROT_CUDA(h, cudaGetLastError());
+    h->prof.kernel_launches += 2;
+    DROT_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+    DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+    const Scalars fin = *h->h_status;
+    iters_done = fin.k;
+
+    h->prof.tile_k = P.K;
+    h->prof.grid_ctas = P.G;
+    h->prof.col_tiles = P.T;
+    h->prof.graph_iters = P.graph_iters;
+
+    drot_status out = DROT_OK;
+    if (done == drot::kIterCap) out = DROT_NOT_CONVERGED;
+    else if (done == drot::kNonFinite) out = DROT_ERR_NONFINITE;
+    if (res) {
+        res->iters = iters_done;
+        res->primal_obj = fin.primal;
+        res->dual_obj = fin.dual;
+        res->gap = fin.gap;
+        res->res_l1 = fin.res_l1;
+        res->res_l2 = fin.res_l2;
+        res->dual_res = fin.dual_res_prev;
+        res->nnz = (int64_t)fin.nnz;
+        res->status = out;
+        if (iters_done == 0) {
+            res->primal_obj = res->dual_obj = res->gap = res->res_l1 = res->res_l2 = res->dual_res = NAN;
+        }
+    }
+    return out;
+}
+
+drot_status check_args(drot_handle *h, long long m, long long n, const float *C, long long ld, const double *p,
+                       const double *q, double tol, long long max_iter, float *X, double *mu, double *nu) {
+    if (!h) return DROT_ERR_INVALID_ARG;
+    if (m < 1 || n < 1) return fail(h, DROT_ERR_INVALID_ARG, "m = %lld and n = %lld must be >= 1", m, n);
+    if (ld < n || ld % 4 != 0) return fail(h, DROT_ERR_INVALID_ARG, "ld = %lld must be >= n and a multiple of 4", ld);
+    if (!C || !p || !q || !X || !mu || !nu) return fail(h, DROT_ERR_INVALID_ARG, "a buffer pointer is NULL");
+    if ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15)
+        return fail(h, DROT_ERR_INVALID_ARG, "C and X must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(mu) |
+         reinterpret_cast<uintptr_t>(nu)) & 7)
+        return fail(h, DROT_ERR_INVALID_ARG, "p, q, mu, nu must be 8-byte aligned");
+    if (max_iter < 0) return fail(h, DROT_ERR_INVALID_ARG, "max_iter = %lld must be >= 0", max_iter);
+    if (std::isnan(tol)) return fail(h, DROT_ERR_INVALID_ARG, "tol is NaN");
+    if (m > (1LL << 40) / n) return fail(h, DROT_ERR_INVALID_ARG, "m * n too large");
+    return DROT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void drot_config_default(drot_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->device = 0;
+    cfg->stream = nullptr;
+    cfg->stop_on_dual_residual = 0;
+    cfg->rho0 = 2.0;
+    cfg->graph_iters = 0;
+    cfg->tile_k = 0;
+    cfg->grid_ctas = 0;
+    cfg->profile = 0;
+}
+
+drot_status drot_create(drot_handle **out, const drot_config *cfg) {
+    if (!out) return DROT_ERR_INVALID_ARG;
+    drot_config c;
+    if (cfg) c = *cfg;
+    else drot_config_default(&c);
+    if (!(c.rho0 > 0.0)) c.rho0 = 2.0;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        cudaGetLastError();
+        return DROT_ERR_CUDA;
+    }
+    if (c.device < 0 || c.device >= ndev) return DROT_ERR_INVALID_ARG;
+    drot_handle *h = new (std::nothrow) drot_handle();
+    if (!h) return DROT_ERR_OOM;
+    h->cfg = c;
+    h->device = c.device;
+    auto bail = [&](drot_status s) {
+        drot_destroy(h);
+        return s;
+    };
+    if (cudaSetDevice(h->device) != cudaSuccess) return bail(DROT_ERR_CUDA);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (c.stream) {
+        h->stream = static_cast<cudaStream_t>(c.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(DROT_ERR_CUDA);
+        h->own_stream = true;
+    }
+    if (cudaMalloc(&h->d_sc, sizeof(Scalars)) != cudaSuccess) return bail(DROT_ERR_OOM);
+    if (cudaMallocHost(&h->h_sc, sizeof(Scalars)) != cudaSuccess) return bail(DROT_ERR_OOM);
+    if (cudaMallocHost(&h->h_status, 2 * sizeof(Scalars)) != cudaSuccess) return bail(DROT_ERR_OOM);
+    std::memset(h->h_status, 0, 2 * sizeof(Scalars));
+    *out = h;
+    return DROT_OK;
+}
+
+drot_status drot_destroy(drot_handle *h) {
+    if (!h) return DROT_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    if (h->work.ptr) cudaFree(h->work.ptr);
+    if (h->staging.ptr) cudaFree(h->staging.ptr);
+    if (h->d_sc) cudaFree(h->d_sc);
+    if (h->h_sc) cudaFreeHost(h->h_sc);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return DROT_OK;
+}
+
+drot_status drot_solve(drot_handle *h, int64_t m, int64_t n, const float *C, int64_t ld, const double *p,
+                       const double *q, double rho, double tol, int64_t max_iter, float *X, double *mu, double *nu,
+                       int warm, drot_result *res) {
+    const auto t0 = std::chrono::steady_clock::now();
+    drot_status st = check_args(h, m, n, C, ld, p, q, tol, max_iter, X, mu, nu);
+    if (st != DROT_OK) return st;
+    h->last_error.clear();
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, DROT_ERR_CUDA, "cudaSetDevice failed");
+    if (!(rho > 0.0)) rho = h->cfg.rho0 / (double)(m + n);
+    if (!std::isfinite(rho)) return fail(h, DROT_ERR_INVALID_ARG, "rho is not finite");
+
+    const void *ptrs[7] = {C, p, q, X, mu, nu, nullptr};
+    int ndev = 0;
+    for (int i = 0; i < 6; ++i) ndev += is_device_ptr(ptrs[i], h->device) ? 1 : 0;
+    if (ndev != 0 && ndev != 6)
+        return fail(h, DROT_ERR_INVALID_ARG, "buffers mix device and host memory (%d of 6 on the device)", ndev);
+
+    if (ndev == 6) {
+        st = solve_device(h, m, n, C, ld, p, q, rho, tol, max_iter, X, mu, nu, warm, res);
+    } else {
+        // host buffers: stage through a device workspace owned by the handle
+        const size_t mat = align_up(sizeof(float) * (size_t)m * ld, 256);
+        const size_t vm = align_up(sizeof(double) * m, 256), vn = align_up(sizeof(double) * n, 256);
+        st = arena_reserve(h, h->staging, 2 * mat + 2 * vm + 2 * vn);
+        if (st != DROT_OK) return st;
+        char *cur = static_cast<char *>(h->staging.ptr);
+        float *dC = carve<float>(cur, (size_t)m * ld);
+        float *dX = carve<float>(cur, (size_t)m * ld);
+        double *dp = carve<double>(cur, m), *dmu = carve<double>(cur, m);
+        double *dq = carve<double>(cur, n), *dnu = carve<double>(cur, n);
+        const size_t mb = sizeof(float) * (size_t)m * ld;
+        DROT_CUDA(h, cudaMemcpyAsync(dC, C, mb, cudaMemcpyHostToDevice, h->stream));
+        DROT_CUDA(h, cudaMemcpyAsync(dp, p, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+        DROT_CUDA(h, cudaMemcpyAsync(dq, q, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        if (warm) {
+            DROT_CUDA(h, cudaMemcpyAsync(dX, X, mb, cudaMemcpyHostToDevice, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(dmu, mu, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(dnu, nu, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        }
+        st = solve_device(h, m, n, dC, ld, dp, dq, rho, tol, max_iter, dX, dmu, dnu, warm, res);
+        if (st == DROT_OK || st == DROT_NOT_CONVERGED || st == DROT_ERR_NONFINITE) {
+            DROT_CUDA(h, cudaMemcpyAsync(X, dX, mb, cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(mu, dmu, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(nu, dnu, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+        }
+    }
+    if (res) res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+drot_status drot_solve_batched(drot_handle *h, int32_t B, const drot_problem *probs, double tol, int64_t max_iter,
+                               int warm, drot_result *res) {
+    if (!h || B < 0 || (B > 0 && !probs)) return DROT_ERR_INVALID_ARG;
+    drot_status first_bad = DROT_OK;
+    for (int32_t b = 0; b < B; ++b) {
+        const drot_problem &P = probs[b];
+        drot_result r{};
+        drot_status st = drot_solve(h, P.m, P.n, P.C, P.ld, P.p, P.q, P.rho, tol, max_iter, P.X, P.mu, P.nu, warm,
+                                    res ? &r : nullptr);
+        if (res) {
+            r.status = st;
+            res[b] = r;
+        }
+        if (st != DROT_OK && first_bad == DROT_OK) first_bad = st;
+        if (st != DROT_OK && st != DROT_NOT_CONVERGED && st != DROT_ERR_NONFINITE) return st;
+    }
+    return first_bad;
+}
+
+drot_status drot_get_profile(drot_handle *h, drot_profile *out) {
+    if (!h || !out) return DROT_ERR_INVALID_ARG;
+    *out = h->prof;
+    return DROT_OK;
+}
+
+drot_status drot_reset_profile(drot_handle *h) {
+    if (!h) return DROT_ERR_INVALID_ARG;
+    const drot_profile keep = h->prof;
+    h->prof = drot_profile{};
+    h->prof.tile_k = keep.tile_k;
+    h->prof.grid_ctas = keep.grid_ctas;
+    h->prof.col_tiles = keep.col_tiles;
+    h->prof.graph_iters = keep.graph_iters;
+    return DROT_OK;
+}
+
+const char *drot_status_string(drot_status s) {
+    switch (s) {
+        case DROT_OK: return "converged";
+        case DROT_ERR_INVALID_ARG: return "invalid argument";
+        case DROT_ERR_MARGINALS: return "invalid marginals";
+        case DROT_ERR_OOM: return "out of memory";
+        case DROT_ERR_CUDA: return "CUDA error";
+        case DROT_NOT_CONVERGED: return "iteration cap reached";
+        case DROT_ERR_TIMEOUT: return "device wait timed out";
+        case DROT_ERR_NONFINITE: return "non-finite value in the iteration";
+    }
+    return "unknown status";
+}
+
+const char *drot_last_error(drot_handle *h) { return h ? h->last_error.c_str() : ""; }
+
+}  // extern "C"

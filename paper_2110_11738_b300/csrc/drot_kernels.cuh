@@ -1,0 +1,511 @@
+// Device code of the DROT solver for sm_103a.
+//
+// One DROT iteration (Algorithm 1, Sec. 3.1) is two launches:
+//
+//   drot_step_kernel    the fused pass over the dense plan: step 4
+//                         x <- max(x + phi_i + psi_j - rho c_ij, 0)
+//                       in place, with the partial reductions the rest of the
+//                       iteration needs taken on the fly (row sums, column sums,
+//                       <C, X_{k+1}>, and ||[phi_k + psi_j - rho C]_+||_F^2 for the
+//                       dual residual of the stopping test, Sec. 3.1).  Each entry
+//                       of X and C is read once and X written once: 12 bytes per
+//                       entry, the whole HBM cost of the iteration.
+//   drot_finish_kernel  the O(m + n) vector work: finishes the row and column sums
+//                       from the per-tile partials, forms r, s, beta and the updates
+//                       of steps 6-8, the stopping quantities, and the convergence
+//                       flag.  The last block to finish (a ticket counter, no
+//                       waiting) does the scalar part.
+//
+// The vectors are carried as FP64 numerators so that the step reads one double
+// per row and per column:  phi_k = (g + c_k) / n,  psi_k = (h + c_k) / m,  with
+// g = a_{k-1} - 2 r_k, h = b_{k-1} - 2 s_k and the scalar c_k = 2 beta_k - alpha_{k-1}
+// (steps 6-7 rewritten).  All cross-thread sums are FP64 and taken in a fixed
+// order, so a solve is bitwise reproducible for a fixed launch plan.
+//
+// Work decomposition of the fused step.  Columns are cut into tiles of
+// TW = 128*K floats (K float4 per lane); a "row segment" is one row of one tile.
+// Segments are numbered tile-major (w = t*m + i) and each CTA takes one
+// contiguous range of segments whose boundaries the host balances by bytes.  Inside
+// a CTA the 8 warps take interleaved rows, so at any time a CTA streams 8
+// neighbouring row segments of X and C with 128-bit coalesced loads.  Row sums
+// are reduced with warp shuffles and written once per segment (rowpart[t][i]);
+// column sums accumulate in registers, are promoted to FP64 in shared memory every
+// few rows, reduced across warps and written once per (CTA, tile) ("slot").
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace drot {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kFlushRows = 16;  // rows per warp between FP32 -> FP64 promotions
+constexpr int kFinishThreads = 256;
+constexpr int kFinishAcc = 6;
+
+enum DoneCode : int { kRunning = 0, kConverged = 1, kIterCap = 2, kNonFinite = 3 };
+
+// Device-resident scalar state of one solve.
+struct Scalars {
+    double c;              // scalar term of phi_k, psi_k (see above)
+    double alpha;          // alpha_k
+    double rho;
+    double tol;
+    double sum_p, sum_q;
+    double min_p, min_q;
+    double sum_phi0, sum_psi0;
+    double primal, dual, gap, res_l1, res_l2, dual_res_prev, beta;
+    long long k;           // iterations completed
+    long long max_iter;
+    int done;              // DoneCode
+    int stop_on_dual;
+    int nonfinite_input;   // set by the marginal check
+    unsigned int counter;  // finish-kernel ticket counter, reset by the last block
+    unsigned long long nnz;
+};
+
+struct StepArgs {
+    const float* C;
+    float* X;
+    const double* g;            // phi numerators (m)
+    const double* h;            // psi numerators (n)
+    const Scalars* sc;
+    double* rowpart;            // [T][m]
+    double* colpart;            // [slots][TW]
+    double* ctapart;            // [G][2]: <C,X> and sum [d]_+^2 per CTA
+    const long long* wbound;    // [G+1] segment range of each CTA
+    const int* slot_base;       // [G]   first slot of each CTA
+    long long m, n, ld;
+    double inv_n, inv_m;
+};
+
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NV doubles in a fixed order; result valid in thread 0.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_f64(double (&v)[NV], double (*scratch)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = warp_sum_f64(v[c]);
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) scratch[warp][c] = v[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += scratch[w][c];
+            v[c] = s;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float4 ld_stream_ro(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+// The fused DR pass (UPDATE = true) or a plain row/column-sum pass over X
+// (UPDATE = false, used once to initialise a_0 and b_0 from the stored X_0).
+template <int K, bool UPDATE>
+__global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
+    constexpr int TW = 128 * K;
+    __shared__ double s_col[kWarps][TW];
+    __shared__ double s_red[kWarps][2];
+
+    if (A.sc->done != kRunning) return;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long m = A.m, n = A.n, ld = A.ld;
+    const long long w0 = A.wbound[blockIdx.x];
+    const long long w1 = A.wbound[blockIdx.x + 1];
+    const float rho = UPDATE ? (float)A.sc->rho : 0.f;
+    const double cs = A.sc->c;
+    int slot = A.slot_base[blockIdx.x];
+    double scx64 = 0.0, sd64 = 0.0;
+
+    long long w = w0;
+    while (w < w1) {
+        const long long t = w / m;
+        const long long seg_end = min(w1, (t + 1) * m);
+        const long long i0 = w - t * m, i1 = seg_end - t * m;
+        const long long col0 = t * TW;
+
+        float psi[K][4], cacc[K][4];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const long long j = col0 + kk * 128 + lane * 4 + e;
+                psi[kk][e] = (UPDATE && j < n) ? (float)((A.h[j] + cs) * A.inv_m) : 0.f;
+                cacc[kk][e] = 0.f;
+            }
+        }
+        for (int x = lane; x < TW; x += 32) s_col[warp][x] = 0.0;
+        __syncwarp();
+
+        float scx = 0.f, sd = 0.f;
+        int since_flush = 0;
+        for (long long i = i0 + warp; i < i1; i += kWarps) {
+            const float phi = UPDATE ? (float)((A.g[i] + cs) * A.inv_n) : 0.f;
+            const long long rowoff = i * ld + col0 + lane * 4;
+            float4 xv[K], cv[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                if (col0 + kk * 128 + lane * 4 < n) {
+                    xv[kk] = *reinterpret_cast<const float4*>(A.X + rowoff + kk * 128);
+                    if (UPDATE) cv[kk] = ld_stream_ro(A.C + rowoff + kk * 128);
+                }
+            }
+            float rs = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const long long j = col0 + kk * 128 + lane * 4;
+                if (j < n) {
+                    float xs[4] = {xv[kk].x, xv[kk].y, xv[kk].z, xv[kk].w};
+                    float cc[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (UPDATE) { cc[0] = cv[kk].x; cc[1] = cv[kk].y; cc[2] = cv[kk].z; cc[3] = cv[kk].w; }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (j + e < n) {
+                            float xn = xs[e];
+                            if (UPDATE) {
+                                const float d = fmaf(-rho, cc[e], phi + psi[kk][e]);
+                                xn = fmaxf(xs[e] + d, 0.f);
+                                scx = fmaf(cc[e], xn, scx);
+                                const float dp = fmaxf(d, 0.f);
+                                sd = fmaf(dp, dp, sd);
+                                xs[e] = xn;
+                            }
+                            rs += xn;
+                            cacc[kk][e] += xn;
+                        }
+                    }
+                    if (UPDATE) {
+                        float* dst = A.X + rowoff + kk * 128;
+                        if (j + 3 < n) {
+                            *reinterpret_cast<float4*>(dst) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (j + e < n) dst[e] = xs[e];
+                        }
+                    }
+                }
+            }
+            rs = warp_sum_f32(rs);
+            if (lane == 0) A.rowpart[t * m + i] = (double)rs;
+            if (++since_flush == kFlushRows) {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        s_col[warp][kk * 128 + lane * 4 + e] += (double)cacc[kk][e];
+                        cacc[kk][e] = 0.f;
+                    }
+                scx64 += (double)scx;
+                sd64 += (double)sd;
+                scx = 0.f;
+                sd = 0.f;
+                since_flush = 0;
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) s_col[warp][kk * 128 + lane * 4 + e] += (double)cacc[kk][e];
+        scx64 += (double)scx;
+        sd64 += (double)sd;
+        __syncthreads();
+        double* out = A.colpart + (long long)slot * TW;
+        for (int x = threadIdx.x; x < TW; x += kThreads) {
+            double v = 0.0;
+#pragma unroll
+            for (int wv = 0; wv < kWarps; ++wv) v += s_col[wv][x];
+            out[x] = v;
+        }
+        __syncthreads();
+        ++slot;
+        w = seg_end;
+    }
+
+    if (UPDATE) {
+        double v[2] = {scx64, sd64};
+        block_sum_f64<2, kThreads>(v, s_red);
+        if (threadIdx.x == 0) {
+            A.ctapart[2 * blockIdx.x + 0] = v[0];
+            A.ctapart[2 * blockIdx.x + 1] = v[1];
+        }
+    }
+}
+
+struct FinishArgs {
+    const double* rowpart;
+    const double* colpart;
+    const double* ctapart;
+    const int* tile_slot;   // [T+1] first slot of each column tile
+    const double* p;
+    const double* q;
+    double* a;
+    double* b;
+    double* g;
+    double* h;
+    double* finpart;        // [gridDim.x][kFinishAcc]
+    Scalars* sc;
+    long long m, n;
+    int T, TW, G;
+    double inv_n, inv_m;
+};
+
+__device__ __forceinline__ double row_total(const FinishArgs& A, long long i) {
+    double u = 0.0;
+    for (int t = 0; t < A.T; ++t) u += A.rowpart[(long long)t * A.m + i];
+    return u;
+}
+
+__device__ __forceinline__ double col_total(const FinishArgs& A, long long j) {
+    const long long t = j / A.TW;
+    const long long jj = j - t * A.TW;
+    double v = 0.0;
+    for (int s = A.tile_slot[t]; s < A.tile_slot[t + 1]; ++s) v += A.colpart[(long long)s * A.TW + jj];
+    return v;
+}
+
+// Returns true in every thread of the block that arrived last (all blocks'
+// finpart rows are then visible).  No block waits for another.
+__device__ __forceinline__ bool arrive_last(Scalars* sc) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int ticket = atomicAdd(&sc->counter, 1u);
+        s_last = (ticket == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1).
+__global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs A) {
+    __shared__ double s_red[kFinishThreads / 32][kFinishAcc];
+    Scalars* sc = A.sc;
+    if (sc->done != kRunning) return;
+
+    // acc: 0 sum r, 1 ||r||_1 + ||s||_1, 2 ||r||^2 + ||s||^2, 3 p.g', 4 q.h', 5 sum s
+    double acc[kFinishAcc] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const long long mn = A.m + A.n;
+    for (long long idx = (long long)blockIdx.x * kFinishThreads + threadIdx.x; idx < mn;
+         idx += (long long)gridDim.x * kFinishThreads) {
+        if (idx < A.m) {
+            const long long i = idx;
+            const double r = row_total(A, i) - A.p[i];
+            const double gn = A.a[i] - 2.0 * r;
+            A.a[i] -= r;
+            A.g[i] = gn;
+            acc[0] += r;
+            acc[1] += fabs(r);
+            acc[2] += r * r;
+            acc[3] += A.p[i] * gn;
+        } else {
+            const long long j = idx - A.m;
+            const double s = col_total(A, j) - A.q[j];
+            const double hn = A.b[j] - 2.0 * s;
+            A.b[j] -= s;
+            A.h[j] = hn;
+            acc[5] += s;
+            acc[1] += fabs(s);
+            acc[2] += s * s;
+            acc[4] += A.q[j] * hn;
+        }
+    }
+    block_sum_f64<kFinishAcc, kFinishThreads>(acc, s_red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < kFinishAcc; ++c) A.finpart[blockIdx.x * kFinishAcc + c] = acc[c];
+    }
+    if (!arrive_last(sc)) return;
+
+    // Last block: fixed-order totals over the blocks of this launch and the
+    // CTAs of the step launch.
+    double tot[kFinishAcc + 2];
+    for (int c = 0; c < kFinishAcc + 2; ++c) tot[c] = 0.0;
+    for (int bidx = threadIdx.x; bidx < (int)gridDim.x; bidx += kFinishThreads)
+        for (int c = 0; c < kFinishAcc; ++c) tot[c] += __ldcg(A.finpart + bidx * kFinishAcc + c);
+    for (int bidx = threadIdx.x; bidx < A.G; bidx += kFinishThreads) {
+        tot[kFinishAcc + 0] += __ldcg(A.ctapart + 2 * bidx + 0);
+        tot[kFinishAcc + 1] += __ldcg(A.ctapart + 2 * bidx + 1);
+    }
+    __shared__ double s_red2[kFinishThreads / 32][kFinishAcc + 2];
+    block_sum_f64<kFinishAcc + 2, kFinishThreads>(tot, s_red2);
+    if (threadIdx.x == 0) {
+        const double mnd = (double)(A.m + A.n);
+        const double beta = tot[0] / mnd;                  // step 5
+        const double c_new = 2.0 * beta - sc->alpha;       // steps 6-7 scalar term
+        const double pphi = (tot[3] + c_new * sc->sum_p) * A.inv_n;
+        const double qpsi = (tot[4] + c_new * sc->sum_q) * A.inv_m;
+        const double rho = sc->rho;
+        const double primal = tot[kFinishAcc + 0];
+        const double dual = (pphi + qpsi) / rho;
+        const double gap = fabs(primal - dual);
+        const double res_l1 = tot[1];
+        const double res_l2 = sqrt(tot[2]);
+        const double dres = sqrt(tot[kFinishAcc + 1]) / rho;
+        sc->alpha -= beta;                                 // step 8
+        sc->c = c_new;
+        sc->beta = beta;
+        sc->primal = primal;
+        sc->dual = dual;
+        sc->gap = gap;
+        sc->res_l1 = res_l1;
+        sc->res_l2 = res_l2;
+        sc->dual_res_prev = dres;
+        const long long k = sc->k + 1;
+        sc->k = k;
+        const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2) &&
+                            isfinite(dres) && isfinite(c_new) && isfinite(tot[5]);
+        bool conv = gap <= sc->tol && res_l1 <= sc->tol;
+        if (sc->stop_on_dual) conv = conv && dres <= sc->tol;
+        int done = kRunning;
+        if (!finite) done = kNonFinite;
+        else if (conv) done = kConverged;
+        else if (k >= sc->max_iter) done = kIterCap;
+        sc->counter = 0u;
+        __threadfence();
+        sc->done = done;
+    }
+}
+
+// ---------------------------------------------------------------- set-up / tear-down
+
+// X_0 = p q^T (the paper's cold start, Sec. 4), rounded to FP32.
+__global__ void drot_init_plan_kernel(float* X, const double* p, const double* q, long long m, long long n,
+                                      long long ld) {
+    const long long nv = (n + 3) / 4;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < m * nv;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / nv;
+        const long long j = (idx - i * nv) * 4;
+        const double pi = p[i];
+        float* dst = X + i * ld + j;
+        if (j + 3 < n) {
+            *reinterpret_cast<float4*>(dst) = make_float4((float)(pi * q[j]), (float)(pi * q[j + 1]),
+                                                          (float)(pi * q[j + 2]), (float)(pi * q[j + 3]));
+        } else {
+            for (int e = 0; e < 4; ++e)
+                if (j + e < n) dst[e] = (float)(pi * q[j + e]);
+        }
+    }
+}
+
+// Sums and minima of the marginals and of the warm-start duals (one block).
+__global__ void __launch_bounds__(1024) drot_vector_sums_kernel(const double* p, const double* q, const double* mu0,
+                                                                const double* nu0, long long m, long long n,
+                                                                Scalars* sc) {
+    __shared__ double s_red[32][6];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // sum p, sum q, sum mu0, sum nu0, bad p, bad q
+    for (long long i = threadIdx.x; i < m; i += blockDim.x) {
+        v[0] += p[i];
+        if (!(p[i] >= 0.0) || !isfinite(p[i])) v[4] += 1.0;
+        if (mu0) v[2] += mu0[i];
+    }
+    for (long long j = threadIdx.x; j < n; j += blockDim.x) {
+        v[1] += q[j];
+        if (!(q[j] >= 0.0) || !isfinite(q[j])) v[5] += 1.0;
+        if (nu0) v[3] += nu0[j];
+    }
+    block_sum_f64<6, 1024>(v, s_red);
+    if (threadIdx.x == 0) {
+        sc->sum_p = v[0];
+        sc->sum_q = v[1];
+        sc->sum_phi0 = sc->rho * v[2];
+        sc->sum_psi0 = sc->rho * v[3];
+        sc->nonfinite_input = (v[4] > 0.0 ? 1 : 0) | (v[5] > 0.0 ? 2 : 0) |
+                              ((isfinite(v[2]) && isfinite(v[3])) ? 0 : 4);
+    }
+}
+
+// a_0 = Y_0 e - p, b_0 = Y_0^T f - q with Y_0 = X_0 + phi_0 e^T + f psi_0^T
+// (Algorithm 1's initialisation, with a warm start phi_0 = rho mu_0,
+// psi_0 = rho nu_0), the numerators g = n phi_0, h = m psi_0, c_0 = 0 and
+// alpha_0 = f^T a_0 / (m + n).  Row and column sums of X_0 come from a
+// preceding UPDATE = false pass of the step kernel.
+__global__ void __launch_bounds__(kFinishThreads) drot_init_state_kernel(FinishArgs A, const double* mu0,
+                                                                         const double* nu0) {
+    __shared__ double s_red[kFinishThreads / 32][1];
+    Scalars* sc = A.sc;
+    const double rho = sc->rho;
+    const double nd = (double)A.n, md = (double)A.m;
+    double acc[1] = {0.0};
+    const long long mn = A.m + A.n;
+    for (long long idx = (long long)blockIdx.x * kFinishThreads + threadIdx.x; idx < mn;
+         idx += (long long)gridDim.x * kFinishThreads) {
+        if (idx < A.m) {
+            const long long i = idx;
+            const double phi0 = mu0 ? rho * mu0[i] : 0.0;
+            const double ai = row_total(A, i) - A.p[i] + nd * phi0 + sc->sum_psi0;
+            A.a[i] = ai;
+            A.g[i] = nd * phi0;
+            acc[0] += ai;
+        } else {
+            const long long j = idx - A.m;
+            const double psi0 = nu0 ? rho * nu0[j] : 0.0;
+            A.b[j] = col_total(A, j) - A.q[j] + md * psi0 + sc->sum_phi0;
+            A.h[j] = md * psi0;
+        }
+    }
+    block_sum_f64<1, kFinishThreads>(acc, s_red);
+    if (threadIdx.x == 0) A.finpart[blockIdx.x * kFinishAcc] = acc[0];
+    if (!arrive_last(sc)) return;
+    double tot[1] = {0.0};
+    for (int bidx = threadIdx.x; bidx < (int)gridDim.x; bidx += kFinishThreads)
+        tot[0] += __ldcg(A.finpart + bidx * kFinishAcc);
+    __shared__ double s_red2[kFinishThreads / 32][1];
+    block_sum_f64<1, kFinishThreads>(tot, s_red2);
+    if (threadIdx.x == 0) {
+        sc->alpha = tot[0] / (md + nd);
+        sc->c = 0.0;
+        sc->k = 0;
+        sc->counter = 0u;
+        sc->done = kRunning;
+    }
+}
+
+// mu = phi / rho, nu = psi / rho (Appendix A.2, eq. dual:var).
+__global__ void drot_export_duals_kernel(const double* g, const double* h, const Scalars* sc, double* mu, double* nu,
+                                         long long m, long long n, double inv_n, double inv_m) {
+    const double c = sc->c, rho = sc->rho;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < m + n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (idx < m) mu[idx] = (g[idx] + c) * inv_n / rho;
+        else nu[idx - m] = (h[idx - m] + c) * inv_m / rho;
+    }
+}
+
+// Number of strictly positive entries of the plan.
+__global__ void drot_count_nnz_kernel(const float* X, long long m, long long n, long long ld, Scalars* sc) {
+    unsigned long long cnt = 0;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < m * n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / n, j = idx - i * n;
+        cnt += X[i * ld + j] > 0.f ? 1ull : 0ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&sc->nnz, cnt);
+}
+
+}  // namespace drot

@@ -1,0 +1,248 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Two kinds of comparison:
+* step parity: both sides start from the same seeded state (X_0, mu_0, nu_0) and
+  run exactly k iterations of Algorithm 1; X_k is compared entry by entry and
+  the duals and stopping quantities value by value;
+* solve parity: both sides run to the stopping test at tol 1e-6; objective,
+  dual objective and residuals are compared (the optimal plan and the duals
+  need not be unique, Prop. 1, so X and the duals are not compared entrywise).
+
+Tolerances follow from FP32 iterates: each entry update x + phi + psi - rho c
+rounds at most a few times at unit roundoff eps32 = 2^-24 of the largest term
+S = max(|x|, |phi|, |psi|, rho |c|), so |x_gpu - x_ref| <= 8 eps32 S per step;
+the row and column sums that feed phi and psi inherit n (or m) such errors and
+are divided by n (m), so mu and nu move by O(eps32 S / rho).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from paper_2110_11738_b300 import drot
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def solver():
+    s = drot.Solver(device=0)
+    yield s
+    s.close()
+
+
+def _dev(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda", dtype=dtype)
+
+
+def _gpu_inputs(pr, X0=None, mu0=None, nu0=None):
+    C = drot.padded_matrix(pr.C, device="cuda")
+    X = torch.zeros_like(C.as_strided((C.shape[0], C.stride(0)), (C.stride(0), 1)))[:, : pr.n]
+    if X0 is not None:
+        X.copy_(torch.as_tensor(X0, dtype=torch.float32))
+    mu = _dev(mu0 if mu0 is not None else np.zeros(pr.m), torch.float64)
+    nu = _dev(nu0 if nu0 is not None else np.zeros(pr.n), torch.float64)
+    return C, _dev(pr.p, torch.float64), _dev(pr.q, torch.float64), X, mu, nu
+
+
+def _step_parity(solver, pr, k, seed):
+    X0, mu0, nu0 = workloads.random_start(pr.m, pr.n, seed)
+    C, p, q, X, mu, nu = _gpu_inputs(pr, X0, mu0, nu0)
+    out = solver.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=k, X=X, mu=mu, nu=nu, warm=True)
+    assert out["status"] == drot.DROT_NOT_CONVERGED and out["iters"] == k
+    ref = oracle.drot_run(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, k, X0=X0.astype(np.float64), mu0=mu0, nu0=nu0)
+    Xg = X.cpu().numpy().astype(np.float64)
+    S = max(np.abs(X0).max(), pr.rho * (np.abs(mu0).max() + np.abs(nu0).max() + 1.0), np.abs(ref["X"]).max())
+    tol_x = 8 * EPS32 * S * k * 4
+    err_x = np.abs(Xg - ref["X"]).max()
+    assert err_x <= tol_x, (err_x, tol_x)
+    assert Xg.min() >= 0.0
+    tol_d = 64 * EPS32 * S / pr.rho * k + 1e-12
+    assert np.abs(mu.cpu().numpy() - ref["mu"]).max() <= tol_d
+    assert np.abs(nu.cpu().numpy() - ref["nu"]).max() <= tol_d
+    h = ref["history"][-1]
+    assert abs(out["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9
+    assert abs(out["res_l1"] - h[oracle.RES_L1]) <= 1e-5 * abs(h[oracle.RES_L1]) + 1e-7
+    assert abs(out["dual_res"] - h[oracle.DUAL_RES_PREV]) <= 1e-4 * abs(h[oracle.DUAL_RES_PREV]) + 1e-6
+    return out
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 5), (3, 7), (33, 129), (130, 257), (257, 1031), (300, 2053),
+                                 (64, 4100), (17, 3)])
+@pytest.mark.parametrize("k", [1, 3])
+def test_step_parity_small_and_ragged(solver, m, n, k):
+    pr = workloads.make_problem("plain_8192x6144", seed=m * 1000 + n, m=m, n=n)
+    _step_parity(solver, pr, k, seed=m + n + k)
+
+
+@pytest.mark.parametrize("tile_k", [1, 2, 4])
+def test_step_parity_every_tile_width(tile_k):
+    pr = workloads.make_problem("plain_256", seed=5, m=203, n=1337)
+    with drot.Solver(device=0, tile_k=tile_k, grid_ctas=37) as s:
+        _step_parity(s, pr, 2, seed=9)
+
+
+def test_step_parity_full_size_8192x6144(solver):
+    pr = workloads.make_problem("plain_8192x6144", seed=0)
+    _step_parity(solver, pr, 2, seed=1)
+
+
+@pytest.mark.slow
+def test_step_parity_full_size_20000(solver):
+    pr = workloads.make_problem("plain_20000", seed=0)
+    _step_parity(solver, pr, 1, seed=2)
+
+
+def _solve_parity(solver, pr, tol=1e-6, rel_obj=1e-5):
+    C, p, q, X, mu, nu = _gpu_inputs(pr)
+    out = solver.solve(C, p, q, rho=pr.rho, tol=tol, max_iter=2_000_000, X=X, mu=mu, nu=nu)
+    assert out["status"] == drot.DROT_OK, out
+    ref = oracle.drot_solve(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, tol, 2_000_000)
+    assert ref["status"] == oracle.STATUS_CONVERGED
+    obj = ref["stats"]["primal"]
+    assert abs(out["primal_obj"] - obj) <= rel_obj * abs(obj)
+    assert abs(out["dual_obj"] - ref["stats"]["dual"]) <= rel_obj * abs(obj)
+    # residuals recomputed in FP64 from the returned plan
+    Xg = X.cpu().numpy().astype(np.float64)
+    st = oracle.plan_stats(pr.C.astype(np.float64), pr.p, pr.q, Xg, mu.cpu().numpy(), nu.cpu().numpy())
+    assert st["res_l1"] <= 1e-6 * 1.5
+    assert abs(st["primal"] - out["primal_obj"]) <= 1e-6 * abs(obj)
+    assert st["gap"] <= 1e-6 * 1.5
+    return out, ref
+
+
+def test_solve_parity_plain_256(solver):
+    pr = workloads.make_problem("plain_256", seed=0)
+    out, ref = _solve_parity(solver, pr)
+    assert 0.5 * ref["iters"] <= out["iters"] <= 2.0 * ref["iters"]
+
+
+@pytest.mark.parametrize("name,m,n", [("warm_1024", 96, 80), ("plain_8192x6144", 130, 47), ("plain_256", 61, 190)])
+def test_solve_parity_other_shapes(solver, name, m, n):
+    pr = workloads.make_problem(name, seed=1, m=m, n=n)
+    _solve_parity(solver, pr)
+
+
+def test_golden_lp_optima(solver):
+    import json
+    import os
+    cases = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "lp_optima.json")))["cases"]
+    for case in cases:
+        pr = workloads.make_problem(case["config"], seed=case["seed"], m=case["m"], n=case["n"])
+        C, p, q, X, mu, nu = _gpu_inputs(pr)
+        out = solver.solve(C, p, q, rho=pr.rho, tol=1e-6, max_iter=2_000_000, X=X, mu=mu, nu=nu)
+        assert out["status"] == drot.DROT_OK
+        opt = case["lp_optimum"]
+        assert abs(out["primal_obj"] - opt) <= 1e-5 * abs(opt) + 2e-6, (case, out["primal_obj"])
+
+
+def test_full_size_8192x6144_certificate(solver):
+    """At the full size the oracle cannot run to convergence; check properties that hold at
+    any size: feasibility in FP64, the reported stats, and a weak-duality lower bound."""
+    pr = workloads.make_problem("plain_8192x6144", seed=0)
+    C, p, q, X, mu, nu = _gpu_inputs(pr)
+    out = solver.solve(C, p, q, rho=pr.rho, tol=1e-6, max_iter=2_000_000, X=X, mu=mu, nu=nu)
+    assert out["status"] == drot.DROT_OK, out
+    Cd = torch.as_tensor(pr.C, device="cuda", dtype=torch.float64)
+    Xd = X.to(torch.float64)
+    pd, qd = p, q
+    res_l1 = float((Xd.sum(1) - pd).abs().sum() + (Xd.sum(0) - qd).abs().sum())
+    primal = float((Cd * Xd).sum())
+    assert float(X.min()) >= 0.0
+    assert res_l1 <= 1.5e-6
+    assert abs(primal - out["primal_obj"]) <= 1e-6 * primal
+    # c-transform of mu: nu'_j = min_i (C_ij - mu_i) makes (mu, nu') dual feasible
+    nu_c = (Cd - mu[:, None]).min(dim=0).values
+    lower = float(pd @ mu + qd @ nu_c)
+    assert lower <= primal + 1e-12
+    assert primal - lower <= 1e-4 * primal, (primal, lower)
+    del Cd, Xd
+
+
+def test_max_iter_zero_returns_cold_start(solver):
+    pr = workloads.make_problem("plain_256", seed=2, m=9, n=13)
+    C, p, q, X, mu, nu = _gpu_inputs(pr)
+    out = solver.solve(C, p, q, rho=pr.rho, tol=1e-6, max_iter=0, X=X, mu=mu, nu=nu)
+    assert out["status"] == drot.DROT_NOT_CONVERGED and out["iters"] == 0
+    ref = np.outer(pr.p, pr.q).astype(np.float32)
+    assert np.array_equal(X.cpu().numpy(), ref)
+
+
+def test_deterministic_bitwise(solver):
+    pr = workloads.make_problem("plain_8192x6144", seed=3, m=700, n=900)
+    outs = []
+    for _ in range(2):
+        C, p, q, X, mu, nu = _gpu_inputs(pr)
+        o = solver.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=50, X=X, mu=mu, nu=nu)
+        outs.append((X.cpu().numpy().copy(), mu.cpu().numpy().copy(), o["primal_obj"], o["gap"]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2] and outs[0][3] == outs[1][3]
+
+
+def test_host_buffers_match_device_buffers(solver):
+    pr = workloads.make_problem("plain_256", seed=4, m=100, n=77)
+    C, p, q, X, mu, nu = _gpu_inputs(pr)
+    od = solver.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=40, X=X, mu=mu, nu=nu)
+    ld = workloads.pad_ld(pr.n)
+    Ch = np.zeros((pr.m, ld), np.float32)
+    Ch[:, : pr.n] = pr.C
+    Xh = np.zeros_like(Ch)
+    muh = np.zeros(pr.m)
+    nuh = np.zeros(pr.n)
+    oh = drot.drot_solve(solver.handle, Ch, pr.p.copy(), pr.q.copy(), rho=pr.rho, tol=-1.0, max_iter=40, X=Xh,
+                         mu=muh, nu=nuh, n=pr.n)
+    assert oh["iters"] == od["iters"] == 40
+    assert np.array_equal(Xh[:, : pr.n], X.cpu().numpy())
+    assert np.array_equal(muh, mu.cpu().numpy())
+
+
+def test_padding_columns_untouched(solver):
+    pr = workloads.make_problem("plain_256", seed=6, m=20, n=29)
+    C, p, q, X, mu, nu = _gpu_inputs(pr)
+    base = X.as_strided((pr.m, X.stride(0)), (X.stride(0), 1))
+    base[:, pr.n:] = 7.0
+    solver.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=5, X=X, mu=mu, nu=nu)
+    assert float(base[:, pr.n:].sub(7.0).abs().max()) == 0.0
+
+
+def test_argument_errors(solver):
+    pr = workloads.make_problem("plain_256", seed=7, m=8, n=8)
+    C, p, q, X, mu, nu = _gpu_inputs(pr)
+    h = solver.handle
+    with pytest.raises(drot.DrotError) as e:
+        drot.drot_solve(h, C, p, q, X=X, mu=mu, nu=nu, max_iter=-1)
+    assert e.value.status == drot.DROT_ERR_INVALID_ARG
+    bad_q = q * 1.01
+    with pytest.raises(drot.DrotError) as e:
+        drot.drot_solve(h, C, p, bad_q, X=X, mu=mu, nu=nu)
+    assert e.value.status == drot.DROT_ERR_MARGINALS
+    neg = p.clone()
+    neg[0] = -neg[0]
+    neg[1] += 2 * p[0]
+    with pytest.raises(drot.DrotError) as e:
+        drot.drot_solve(h, C, neg, q, X=X, mu=mu, nu=nu)
+    assert e.value.status == drot.DROT_ERR_MARGINALS
+    # unaligned C: offset the base by one float
+    raw = torch.zeros(8 * 8 + 1, device="cuda", dtype=torch.float32)
+    Cu = raw[1:].view(8, 8)
+    with pytest.raises(drot.DrotError) as e:
+        drot.drot_solve(h, Cu, p, q, X=X, mu=mu, nu=nu)
+    assert e.value.status == drot.DROT_ERR_INVALID_ARG
+    # mixed host/device buffers
+    with pytest.raises(drot.DrotError) as e:
+        drot.drot_solve(h, C, pr.p.copy(), q, X=X, mu=mu, nu=nu)
+    assert e.value.status == drot.DROT_ERR_INVALID_ARG
+
+
+def test_nonfinite_cost_is_reported(solver):
+    pr = workloads.make_problem("plain_256", seed=8, m=16, n=16)
+    C, p, q, X, mu, nu = _gpu_inputs(pr)
+    C[3, 5] = float("nan")
+    out = drot.drot_solve(solver.handle, C, p, q, rho=pr.rho, tol=1e-6, max_iter=100, X=X, mu=mu, nu=nu,
+                          check=False)
+    assert out["status"] == drot.DROT_ERR_NONFINITE
+    assert out["iters"] == 1
