@@ -19,11 +19,11 @@
  * returned are mu = phi / rho and nu = psi / rho (Appendix A.2, eq. dual:var).
  *
  * Stopping test (Sec. 3.1, "Stopping criteria"), evaluated on the device after every
- * iteration: stop when gap <= tol and ||r||_1 + ||s||_1 <= tol, where
- * gap = |<C, X_k> - (p^T phi_k + q^T psi_k)/rho|; if stop_on_dual_residual is set, also
- * require r_dual = ||[(phi/rho) 1^T + 1 (psi/rho)^T - C]_+||_F <= tol.  r_dual of
- * (phi_k, psi_k) is produced by the pass that computes X_{k+1}, so the test uses the
- * value from the same pass (one iteration older than gap and residuals).
+ * iteration on the quantities selected by drot_config.stop_rule (default: gap and l1
+ * residual): gap = |<C, X_k> - (p^T phi_k + q^T psi_k)/rho| <= tol,
+ * ||r||_1 + ||s||_1 <= tol, r_dual = ||[(phi/rho) 1^T + 1 (psi/rho)^T - C]_+||_F <= tol.
+ * r_dual of (phi_k, psi_k) is produced by the pass that computes X_{k+1}, so the test
+ * uses the value from the same pass (one iteration older than gap and residuals).
  *
  * Data layout: C and X are dense row-major FP32 m x n matrices with row pitch ld
  * (floats): entry (i, j) lives at base[i*ld + j].  ld must be >= n and a multiple of 4,
@@ -70,10 +70,15 @@ typedef enum {
     DROT_ERR_NONFINITE = 7      /* a NaN/Inf appeared in the iteration; outputs hold the last iterate */
 } drot_status;
 
+/* Quantities that gate the stopping test (bitmask, drot_config.stop_rule). */
+#define DROT_STOP_GAP 1       /* |<C,X> - (p^T phi + q^T psi)/rho| <= tol */
+#define DROT_STOP_RES_L1 2    /* ||X 1 - p||_1 + ||X^T 1 - q||_1 <= tol */
+#define DROT_STOP_DUAL_RES 4  /* ||[(phi/rho) 1^T + 1 (psi/rho)^T - C]_+||_F <= tol */
+
 typedef struct {
     int device;                 /* CUDA device ordinal (default 0) */
     void *stream;               /* cudaStream_t to issue work on; NULL: the handle creates one */
-    int stop_on_dual_residual;  /* 1: the stopping test also requires r_dual <= tol (default 0) */
+    int stop_rule;              /* bitmask of DROT_STOP_*; 0 selects DROT_STOP_GAP | DROT_STOP_RES_L1 */
     double rho0;                /* rho = rho0 / (m + n) when a call passes rho <= 0 (default 2, Sec. 4) */
     int graph_iters;            /* iterations per CUDA-graph replay; 0: chosen from the problem size */
     int tile_k;                 /* float4 chunks per lane per row segment (1, 2 or 4); 0: automatic */

@@ -90,10 +90,11 @@ def set_mutation(k: int) -> None:
 
 
 def drot_solve(C, p, q, rho, tol, max_iter, X0=None, mu0=None, nu0=None,
-               stop_on_dual_residual=False, history=False):
+               stop_on_dual_residual=False, history=False, stop_rule=None):
     """Run Algorithm 1 from X0 = p q^T (or from a warm start) until the stop rule.
 
-    Returns a dict with X, mu, nu (FP64), iters, status, stats (dict) and,
+    ``stop_rule`` is a bitmask (1 gap, 2 l1 residual, 4 r_dual; default 3, or 7 with
+    ``stop_on_dual_residual``).  Returns a dict with X, mu, nu (FP64), iters, status, stats (dict) and,
     when ``history`` is true, the per-iteration stats as an (iters, 7) array.
     """
     lib = _load()
@@ -109,7 +110,7 @@ def drot_solve(C, p, q, rho, tol, max_iter, X0=None, mu0=None, nu0=None,
     iters = ctypes.c_int64(0)
     hist = np.zeros((max(int(max_iter), 1), NSTATS)) if history else None
     rc = lib.oracle_solve(m, n, _ptr(C), _ptr(p), _ptr(q), float(rho), float(tol), int(max_iter),
-                          int(bool(stop_on_dual_residual)), int(warm), _ptr(X), _ptr(mu), _ptr(nu),
+                          int(stop_rule if stop_rule is not None else (7 if stop_on_dual_residual else 3)), int(warm), _ptr(X), _ptr(mu), _ptr(nu),
                           _ptr(stats), ctypes.byref(iters),
                           _ptr(hist) if hist is not None else ctypes.POINTER(ctypes.c_double)())
     if rc < 0:

@@ -29,7 +29,7 @@
  * r_dual for (phi_k, psi_k) needs one pass over C with those vectors; the
  * pass that produces X_{k+1} is that pass, so each iteration reports r_dual of
  * the vectors it started from ("lagged").  The stop rule is: gap <= tol and
- * l1 residual <= tol, and, when requested, the lagged r_dual <= tol.
+ * l1 residual <= tol (optionally, by a bitmask: 1 gap, 2 l1 residual, 4 lagged r_dual).
  *
  * Initial state (Algorithm 1, lines before the loop, generalised to a warm
  * start): Y_0 = X_0 + phi_0 e^T + f psi_0^T, a_0 = Y_0 e - p,
@@ -175,7 +175,7 @@ void oracle_iterate(int64_t m, int64_t n, const double *C, const double *p, cons
  * iteration.  Returns 0 when the stop rule fired, 1 when max_iter ran out,
  * 2 on a non-finite value, -1 on bad arguments or allocation failure. */
 int oracle_solve(int64_t m, int64_t n, const double *C, const double *p, const double *q,
-                 double rho, double tol, int64_t max_iter, int stop_on_dual_residual, int warm,
+                 double rho, double tol, int64_t max_iter, int stop_rule, int warm,
                  double *X, double *mu, double *nu, double *stats, int64_t *iters, double *history)
 {
     if (m <= 0 || n <= 0 || !(rho > 0.0) || max_iter < 0) return -1;
@@ -210,8 +210,9 @@ int oracle_solve(int64_t m, int64_t n, const double *C, const double *p, const d
         int finite = 1;
         for (int i = 0; i < ORC_NSTATS; ++i) finite &= isfinite(stats[i]) ? 1 : 0;
         if (!finite) { rc = 2; break; }
-        int done = stats[ORC_GAP] <= tol && stats[ORC_RES_L1] <= tol;
-        if (stop_on_dual_residual) done = done && stats[ORC_DUAL_RES_PREV] <= tol;
+        int rule = (stop_rule & 7) ? (stop_rule & 7) : 3;
+        int done = (!(rule & 1) || stats[ORC_GAP] <= tol) && (!(rule & 2) || stats[ORC_RES_L1] <= tol) &&
+                   (!(rule & 4) || stats[ORC_DUAL_RES_PREV] <= tol);
         if (done) { rc = 0; break; }
     }
     for (int64_t i = 0; i < m; ++i) mu[i] = phi[i] / rho;

@@ -348,7 +348,7 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     S.rho = rho;
     S.tol = tol;
     S.max_iter = max_iter;
-    S.stop_on_dual = h->cfg.stop_on_dual_residual ? 1 : 0;
+    S.stop_rule = (h->cfg.stop_rule & 7) ? (h->cfg.stop_rule & 7) : (DROT_STOP_GAP | DROT_STOP_RES_L1);
     S.done = drot::kRunning;
     DROT_CUDA(h, cudaMemcpyAsync(h->d_sc, &S, sizeof S, cudaMemcpyHostToDevice, h->stream));
     drot::drot_vector_sums_kernel<<<1, 1024, 0, h->stream>>>(p, q, warm ? mu : nullptr, warm ? nu : nullptr, m, n,
@@ -517,7 +517,7 @@ void drot_config_default(drot_config *cfg) {
     std::memset(cfg, 0, sizeof *cfg);
     cfg->device = 0;
     cfg->stream = nullptr;
-    cfg->stop_on_dual_residual = 0;
+    cfg->stop_rule = DROT_STOP_GAP | DROT_STOP_RES_L1;
     cfg->rho0 = 2.0;
     cfg->graph_iters = 0;
     cfg->tile_k = 0;

@@ -59,7 +59,7 @@ struct Scalars {
     long long k;           // iterations completed
     long long max_iter;
     int done;              // DoneCode
-    int stop_on_dual;
+    int stop_rule;         // DROT_STOP_* bitmask (never 0)
     int nonfinite_input;   // set by the marginal check
     unsigned int counter;  // finish-kernel ticket counter, reset by the last block
     unsigned long long nnz;
@@ -271,18 +271,40 @@ struct FinishArgs {
     double inv_n, inv_m;
 };
 
+// Sum of `count` partials spaced `stride` apart, in a fixed order: four
+// interleaved accumulators (so that up to eight loads are in flight), combined
+// as (a0 + a1) + (a2 + a3).
+__device__ __forceinline__ double strided_total(const double* base, long long stride, int count) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int t = 0;
+    for (; t + 8 <= count; t += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = base[(long long)(t + u) * stride];
+        a0 += v[0]; a1 += v[1]; a2 += v[2]; a3 += v[3];
+        a0 += v[4]; a1 += v[5]; a2 += v[6]; a3 += v[7];
+    }
+    for (; t < count; ++t) {
+        const double v = base[(long long)t * stride];
+        switch (t & 3) {
+            case 0: a0 += v; break;
+            case 1: a1 += v; break;
+            case 2: a2 += v; break;
+            default: a3 += v; break;
+        }
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
 __device__ __forceinline__ double row_total(const FinishArgs& A, long long i) {
-    double u = 0.0;
-    for (int t = 0; t < A.T; ++t) u += A.rowpart[(long long)t * A.m + i];
-    return u;
+    return strided_total(A.rowpart + i, A.m, A.T);
 }
 
 __device__ __forceinline__ double col_total(const FinishArgs& A, long long j) {
     const long long t = j / A.TW;
     const long long jj = j - t * A.TW;
-    double v = 0.0;
-    for (int s = A.tile_slot[t]; s < A.tile_slot[t + 1]; ++s) v += A.colpart[(long long)s * A.TW + jj];
-    return v;
+    const int s0 = A.tile_slot[t];
+    return strided_total(A.colpart + (long long)s0 * A.TW + jj, A.TW, A.tile_slot[t + 1] - s0);
 }
 
 // Returns true in every thread of the block that arrived last (all blocks'
@@ -378,8 +400,9 @@ __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs 
         sc->k = k;
         const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2) &&
                             isfinite(dres) && isfinite(c_new) && isfinite(tot[5]);
-        bool conv = gap <= sc->tol && res_l1 <= sc->tol;
-        if (sc->stop_on_dual) conv = conv && dres <= sc->tol;
+        const int rule = sc->stop_rule;
+        const bool conv = (!(rule & 1) || gap <= sc->tol) && (!(rule & 2) || res_l1 <= sc->tol) &&
+                          (!(rule & 4) || dres <= sc->tol);
         int done = kRunning;
         if (!finite) done = kNonFinite;
         else if (conv) done = kConverged;

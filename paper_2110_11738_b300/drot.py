@@ -41,7 +41,7 @@ EXPORTED = ("drot_config_default", "drot_create", "drot_solve", "drot_solve_batc
 
 
 class DrotConfig(ctypes.Structure):
-    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("stop_on_dual_residual", ctypes.c_int),
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("stop_rule", ctypes.c_int),
                 ("rho0", ctypes.c_double), ("graph_iters", ctypes.c_int), ("tile_k", ctypes.c_int),
                 ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int)]
 
@@ -124,7 +124,12 @@ def _result_dict(r: DrotResult) -> dict:
 
 # ---------------------------------------------------------------- C-named entry points
 
-def drot_create(device: int = 0, stream: Optional[int] = None, stop_on_dual_residual: bool = False,
+STOP_GAP = 1
+STOP_RES_L1 = 2
+STOP_DUAL_RES = 4
+
+
+def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = STOP_GAP | STOP_RES_L1,
                 rho0: float = 2.0, graph_iters: int = 0, tile_k: int = 0, grid_ctas: int = 0,
                 profile: bool = False) -> int:
     """Create a solver handle; returns the opaque handle as an int."""
@@ -133,7 +138,7 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_on_dual_resi
     lib.drot_config_default(ctypes.byref(cfg))
     cfg.device = int(device)
     cfg.stream = int(stream) if stream else None
-    cfg.stop_on_dual_residual = int(bool(stop_on_dual_residual))
+    cfg.stop_rule = int(stop_rule)
     cfg.rho0 = float(rho0)
     cfg.graph_iters = int(graph_iters)
     cfg.tile_k = int(tile_k)
