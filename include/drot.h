@@ -84,6 +84,8 @@ typedef struct {
     int tile_k;                 /* float4 chunks per lane per row segment (1, 2 or 4); 0: automatic */
     int grid_ctas;              /* CTAs of the fused step kernel; 0: automatic */
     int profile;                /* 1: time every fused-step launch with CUDA events (drot_get_profile) */
+    int step_variant;           /* fused step: 1 register-fed (128-bit loads), 2 TMA-fed (bulk copies into a
+                                   shared-memory ring); 0: automatic */
 } drot_config;
 
 typedef struct {
@@ -115,6 +117,7 @@ typedef struct {
     int64_t kernel_launches;    /* all kernels this handle launched (including early exits) */
     int64_t graph_replays;      /* CUDA-graph replays issued */
     int32_t tile_k, grid_ctas, col_tiles, graph_iters;  /* the plan of the last solve */
+    int32_t step_variant, stages;                       /* fused-step variant and ring depth used */
 } drot_profile;
 
 /* Fill cfg with the defaults listed above. */

@@ -27,6 +27,7 @@ namespace {
 
 struct Plan {
     int K = 4, TW = 512, T = 1, G = 1, slots = 1, fin_blocks = 1, graph_iters = 1;
+    int variant = 1, S = 0;  // fused-step variant (1 register-fed, 2 TMA-fed) and ring stages
     std::vector<long long> wbound;  // G+1
     std::vector<int> slot_base;     // G
     std::vector<int> tile_slot;     // T+1
@@ -36,10 +37,11 @@ struct GraphKey {
     long long m = -1, n = -1, ld = -1;
     const void *C = nullptr, *X = nullptr, *p = nullptr, *q = nullptr;
     const void *arena = nullptr;
-    int K = 0, G = 0, graph_iters = 0, profile = 0;
+    int K = 0, G = 0, graph_iters = 0, profile = 0, variant = 0;
     bool operator==(const GraphKey &o) const {
         return m == o.m && n == o.n && ld == o.ld && C == o.C && X == o.X && p == o.p && q == o.q &&
-               arena == o.arena && K == o.K && G == o.G && graph_iters == o.graph_iters && profile == o.profile;
+               arena == o.arena && K == o.K && G == o.G && graph_iters == o.graph_iters && profile == o.profile &&
+               variant == o.variant;
     }
 };
 
@@ -49,6 +51,30 @@ struct Arena {
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Ring depth of the TMA-fed step for a tile width (each stage holds 8 rows of X and C).
+int tma_stages(int K) { return K == 4 ? 4 : (K == 2 ? 8 : 16); }
+
+template <int K, int S>
+cudaError_t set_tma_attr() {
+    return cudaFuncSetAttribute(drot::drot_step_tma_kernel<K, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)drot::TmaLayout<K, S>::bytes);
+}
+
+// Opt the TMA-fed kernels into their shared-memory ring size on the current device
+// (done once per handle, outside any stream capture).
+cudaError_t set_kernel_attributes() {
+    cudaError_t e = set_tma_attr<1, 16>();
+    if (e == cudaSuccess) e = set_tma_attr<2, 8>();
+    if (e == cudaSuccess) e = set_tma_attr<4, 4>();
+    return e;
+}
+
+template <int K, int S>
+cudaError_t launch_tma(int G, const drot::StepArgs &A, cudaStream_t s) {
+    drot::drot_step_tma_kernel<K, S><<<G, drot::kThreads + 32, drot::TmaLayout<K, S>::bytes, s>>>(A);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -141,11 +167,17 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P) {
     P.TW = 128 * K;
     P.T = (int)((n + P.TW - 1) / P.TW);
     const long long units = (long long)P.T * m;
+    int variant = h->cfg.step_variant;
+    if (variant != 1 && variant != 2) variant = 1;
+    P.variant = variant;
+    P.S = variant == 2 ? tma_stages(K) : 0;
     int G = h->cfg.grid_ctas;
     if (G <= 0) {
-        // two resident CTAs per SM; small problems use fewer CTAs so each warp has rows
+        // register-fed: two resident CTAs per SM; TMA-fed: one CTA (and one ring) per SM.
+        // Small problems use fewer CTAs so that each warp has rows.
         const long long want = (units + drot::kWarps - 1) / drot::kWarps;
-        G = (int)std::min<long long>(2LL * h->num_sms, std::max<long long>(1, want));
+        const long long per_sm = variant == 2 ? 1 : 2;
+        G = (int)std::min<long long>(per_sm * h->num_sms, std::max<long long>(1, want));
     }
     G = (int)std::min<long long>(G, std::max<long long>(1, units));
     P.G = G;
@@ -278,6 +310,13 @@ drot::FinishArgs finish_args(const drot_handle *h, long long m, long long n, con
 
 template <bool UPDATE>
 cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s) {
+    if (UPDATE && P.variant == 2) {
+        switch (P.K) {
+            case 1: return launch_tma<1, 16>(P.G, A, s);
+            case 2: return launch_tma<2, 8>(P.G, A, s);
+            default: return launch_tma<4, 4>(P.G, A, s);
+        }
+    }
     switch (P.K) {
         case 1: drot::drot_step_kernel<1, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
         case 2: drot::drot_step_kernel<2, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
@@ -386,6 +425,7 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
         GraphKey key;
         key.m = m; key.n = n; key.ld = ld; key.C = C; key.X = X; key.p = p; key.q = q;
         key.arena = h->work.ptr; key.K = P.K; key.G = P.G; key.graph_iters = P.graph_iters;
+        key.variant = P.variant;
         key.profile = h->cfg.profile ? 1 : 0;
         if (!(key == h->key) || !h->exec[0]) {
             st = build_graphs(h, key, P, A, F);
@@ -470,10 +510,13 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     h->prof.grid_ctas = P.G;
     h->prof.col_tiles = P.T;
     h->prof.graph_iters = P.graph_iters;
+    h->prof.step_variant = P.variant;
+    h->prof.stages = P.S;
 
     drot_status out = DROT_OK;
     if (done == drot::kIterCap) out = DROT_NOT_CONVERGED;
     else if (done == drot::kNonFinite) out = DROT_ERR_NONFINITE;
+    else if (done == drot::kFault) out = DROT_ERR_TIMEOUT;
     if (res) {
         res->iters = iters_done;
         res->primal_obj = fin.primal;
@@ -523,6 +566,7 @@ void drot_config_default(drot_config *cfg) {
     cfg->tile_k = 0;
     cfg->grid_ctas = 0;
     cfg->profile = 0;
+    cfg->step_variant = 0;
 }
 
 drot_status drot_create(drot_handle **out, const drot_config *cfg) {
@@ -547,6 +591,7 @@ drot_status drot_create(drot_handle **out, const drot_config *cfg) {
     };
     if (cudaSetDevice(h->device) != cudaSuccess) return bail(DROT_ERR_CUDA);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (set_kernel_attributes() != cudaSuccess) return bail(DROT_ERR_CUDA);
     if (c.stream) {
         h->stream = static_cast<cudaStream_t>(c.stream);
     } else {
@@ -657,6 +702,8 @@ drot_status drot_reset_profile(drot_handle *h) {
     const drot_profile keep = h->prof;
     h->prof = drot_profile{};
     h->prof.tile_k = keep.tile_k;
+    h->prof.step_variant = keep.step_variant;
+    h->prof.stages = keep.stages;
     h->prof.grid_ctas = keep.grid_ctas;
     h->prof.col_tiles = keep.col_tiles;
     h->prof.graph_iters = keep.graph_iters;

@@ -44,7 +44,7 @@ constexpr int kFlushRows = 16;  // rows per warp between FP32 -> FP64 promotions
 constexpr int kFinishThreads = 256;
 constexpr int kFinishAcc = 6;
 
-enum DoneCode : int { kRunning = 0, kConverged = 1, kIterCap = 2, kNonFinite = 3 };
+enum DoneCode : int { kRunning = 0, kConverged = 1, kIterCap = 2, kNonFinite = 3, kFault = 4 };
 
 // Device-resident scalar state of one solve.
 struct Scalars {
@@ -62,6 +62,7 @@ struct Scalars {
     int stop_rule;         // DROT_STOP_* bitmask (never 0)
     int nonfinite_input;   // set by the marginal check
     unsigned int counter;  // finish-kernel ticket counter, reset by the last block
+    int fault;             // set when a bounded device-side wait gave up
     unsigned long long nnz;
 };
 
@@ -253,6 +254,285 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
     }
 }
 
+
+// ------------------------------------------------------------------ TMA-fed variant
+//
+// Same arithmetic, partials and work split as drot_step_kernel<K, true>, but the
+// row segments of X and C reach shared memory through 1-D bulk copies
+// (cp.async.bulk, the TMA engine) into an S-stage ring, so the bytes in flight per
+// SM do not depend on registers or occupancy.  One producer warp (one elected
+// lane) issues the copies of 8 row segments per stage and signals a "full"
+// mbarrier with the byte count; the 8 consumer warps each take one row of the
+// stage, compute x+ from shared memory, store it to global memory with 128-bit
+// stores, and arrive on the stage's "empty" mbarrier.  Every wait is bounded:
+// after kWaitLimit polls the kernel records a fault in Scalars and returns.
+
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete; false on timeout
+// or when another warp of the block has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 1023u) == 1023u && *abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+}
+
+template <int K, int S>
+struct TmaLayout {
+    static constexpr int TW = 128 * K;
+    static constexpr size_t stage_floats = (size_t)kWarps * TW;
+    static constexpr size_t bytes = 2 * S * stage_floats * sizeof(float)   // X and C rings
+                                    + (size_t)kWarps * TW * sizeof(double)  // column accumulators
+                                    + 2 * S * sizeof(uint64_t);             // full / empty barriers
+};
+
+template <int K, int S>
+__global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArgs A) {
+    constexpr int TW = 128 * K;
+    constexpr int R = kWarps;  // rows per stage, one per consumer warp
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* sX = reinterpret_cast<float*>(smem_raw);
+    float* sC = sX + (size_t)S * R * TW;
+    double* s_col = reinterpret_cast<double*>(sC + (size_t)S * R * TW);
+    uint64_t* full = reinterpret_cast<uint64_t*>(s_col + kWarps * TW);
+    uint64_t* empty = full + S;
+    __shared__ double s_red[kWarps + 1][2];
+    __shared__ int s_abort;
+    __shared__ uint32_t s_issued;
+
+    if (A.sc->done != kRunning) return;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long m = A.m, n = A.n, ld = A.ld;
+    const long long w0 = A.wbound[blockIdx.x];
+    const long long w1 = A.wbound[blockIdx.x + 1];
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], kWarps);
+        }
+        s_abort = 0;
+        s_issued = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    double scx64 = 0.0, sd64 = 0.0;
+    bool ok = true;
+
+    if (warp == kWarps) {
+        // ---------------- producer: one lane issues every bulk copy
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (long long w = w0; w < w1 && ok;) {
+                const long long t = w / m;
+                const long long seg_end = min(w1, (t + 1) * m);
+                const long long i0 = w - t * m, i1 = seg_end - t * m;
+                const long long col0 = t * TW;
+                const long long cols = min((long long)TW, n - col0);
+                const uint32_t bytes = (uint32_t)(((cols + 3) / 4) * 16);
+                for (long long r0 = i0; r0 < i1; r0 += R, ++g) {
+                    const int st = (int)(g % S);
+                    const uint32_t use = g / S;
+                    if (!mbar_wait(&empty[st], (use & 1u) ^ 1u, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const int rows = (int)min((long long)R, i1 - r0);
+                    mbar_arrive_expect_tx(&full[st], (uint32_t)rows * 2u * bytes);
+                    for (int rr = 0; rr < rows; ++rr) {
+                        const long long off = (r0 + rr) * ld + col0;
+                        bulk_load(sX + ((size_t)st * R + rr) * TW, A.X + off, bytes, &full[st]);
+                        bulk_load(sC + ((size_t)st * R + rr) * TW, A.C + off, bytes, &full[st]);
+                    }
+                }
+                w = seg_end;
+            }
+            s_issued = g;
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(const_cast<int*>(&A.sc->fault), 1);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- consumers
+        const double cs = A.sc->c;
+        const float rho = (float)A.sc->rho;
+        int slot = A.slot_base[blockIdx.x];
+        uint32_t g = 0;
+        for (long long w = w0; w < w1;) {
+            const long long t = w / m;
+            const long long seg_end = min(w1, (t + 1) * m);
+            const long long i0 = w - t * m, i1 = seg_end - t * m;
+            const long long col0 = t * TW;
+
+            float psi[K][4], cacc[K][4];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const long long j = col0 + kk * 128 + lane * 4 + e;
+                    psi[kk][e] = j < n ? (float)((A.h[j] + cs) * A.inv_m) : 0.f;
+                    cacc[kk][e] = 0.f;
+                }
+            for (int x = lane; x < TW; x += 32) s_col[warp * TW + x] = 0.0;
+            __syncwarp();
+
+            float scx = 0.f, sd = 0.f;
+            int since_flush = 0;
+            for (long long r0 = i0; r0 < i1; r0 += R, ++g) {
+                const int st = (int)(g % S);
+                const uint32_t use = g / S;
+                if (ok && !mbar_wait(&full[st], use & 1u, &s_abort)) {
+                    ok = false;
+                    if (lane == 0) {
+                        s_abort = 1;
+                        atomicExch(const_cast<int*>(&A.sc->fault), 1);
+                    }
+                }
+                const long long i = r0 + warp;
+                if (ok && i < i1) {
+                    const float phi = (float)((A.g[i] + cs) * A.inv_n);
+                    const float* xs_row = sX + ((size_t)st * R + warp) * TW;
+                    const float* cs_row = sC + ((size_t)st * R + warp) * TW;
+                    float* dst_row = A.X + i * ld + col0;
+                    float rs = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        const int jl = kk * 128 + lane * 4;
+                        const long long j = col0 + jl;
+                        if (j < n) {
+                            const float4 xv = *reinterpret_cast<const float4*>(xs_row + jl);
+                            const float4 cv = *reinterpret_cast<const float4*>(cs_row + jl);
+                            float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+                            const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                if (j + e < n) {
+                                    const float d = fmaf(-rho, cc[e], phi + psi[kk][e]);
+                                    const float xn = fmaxf(xs[e] + d, 0.f);
+                                    scx = fmaf(cc[e], xn, scx);
+                                    const float dp = fmaxf(d, 0.f);
+                                    sd = fmaf(dp, dp, sd);
+                                    xs[e] = xn;
+                                    rs += xn;
+                                    cacc[kk][e] += xn;
+                                }
+                            }
+                            if (j + 3 < n) {
+                                *reinterpret_cast<float4*>(dst_row + jl) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    if (j + e < n) dst_row[jl + e] = xs[e];
+                            }
+                        }
+                    }
+                    rs = warp_sum_f32(rs);
+                    if (lane == 0) A.rowpart[t * m + i] = (double)rs;
+                    if (++since_flush == kFlushRows) {
+#pragma unroll
+                        for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                s_col[warp * TW + kk * 128 + lane * 4 + e] += (double)cacc[kk][e];
+                                cacc[kk][e] = 0.f;
+                            }
+                        scx64 += (double)scx;
+                        sd64 += (double)sd;
+                        scx = 0.f;
+                        sd = 0.f;
+                        since_flush = 0;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[st]);
+            }
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) s_col[warp * TW + kk * 128 + lane * 4 + e] += (double)cacc[kk][e];
+            scx64 += (double)scx;
+            sd64 += (double)sd;
+            consumer_sync();
+            double* out = A.colpart + (long long)slot * TW;
+            for (int x = threadIdx.x; x < TW; x += kThreads) {
+                double v = 0.0;
+#pragma unroll
+                for (int wv = 0; wv < kWarps; ++wv) v += s_col[wv * TW + x];
+                out[x] = v;
+            }
+            consumer_sync();
+            ++slot;
+            w = seg_end;
+        }
+    }
+
+    double v[2] = {scx64, sd64};
+    block_sum_f64<2, kThreads + 32>(v, s_red);
+    if (threadIdx.x == 0) {
+        A.ctapart[2 * blockIdx.x + 0] = v[0];
+        A.ctapart[2 * blockIdx.x + 1] = v[1];
+        if (s_abort) {
+            // after a give-up, let the copies already issued land before the
+            // block's shared memory is released (each wait bounded as well)
+            const uint32_t last = s_issued;
+            for (uint32_t u = last > (uint32_t)S ? last - S : 0u; u < last; ++u)
+                for (uint32_t it = 0; it < kWaitLimit; ++it)
+                    if (mbar_try_wait(&full[u % S], (u / S) & 1u)) break;
+        }
+    }
+}
+
 struct FinishArgs {
     const double* rowpart;
     const double* colpart;
@@ -404,7 +684,8 @@ __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs 
         const bool conv = (!(rule & 1) || gap <= sc->tol) && (!(rule & 2) || res_l1 <= sc->tol) &&
                           (!(rule & 4) || dres <= sc->tol);
         int done = kRunning;
-        if (!finite) done = kNonFinite;
+        if (sc->fault) done = kFault;
+        else if (!finite) done = kNonFinite;
         else if (conv) done = kConverged;
         else if (k >= sc->max_iter) done = kIterCap;
         sc->counter = 0u;

@@ -43,7 +43,7 @@ EXPORTED = ("drot_config_default", "drot_create", "drot_solve", "drot_solve_batc
 class DrotConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("stop_rule", ctypes.c_int),
                 ("rho0", ctypes.c_double), ("graph_iters", ctypes.c_int), ("tile_k", ctypes.c_int),
-                ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int), ("step_variant", ctypes.c_int)]
 
 
 class DrotResult(ctypes.Structure):
@@ -63,7 +63,7 @@ class DrotProfile(ctypes.Structure):
     _fields_ = [("step_ms_total", ctypes.c_double), ("step_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("tile_k", ctypes.c_int32), ("grid_ctas", ctypes.c_int32), ("col_tiles", ctypes.c_int32),
-                ("graph_iters", ctypes.c_int32)]
+                ("graph_iters", ctypes.c_int32), ("step_variant", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
 class DrotError(RuntimeError):
@@ -131,7 +131,7 @@ STOP_DUAL_RES = 4
 
 def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = STOP_GAP | STOP_RES_L1,
                 rho0: float = 2.0, graph_iters: int = 0, tile_k: int = 0, grid_ctas: int = 0,
-                profile: bool = False) -> int:
+                profile: bool = False, step_variant: int = 0) -> int:
     """Create a solver handle; returns the opaque handle as an int."""
     lib = load()
     cfg = DrotConfig()
@@ -144,6 +144,7 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
     cfg.tile_k = int(tile_k)
     cfg.grid_ctas = int(grid_ctas)
     cfg.profile = int(bool(profile))
+    cfg.step_variant = int(step_variant)
     h = ctypes.c_void_p()
     st = lib.drot_create(ctypes.byref(h), ctypes.byref(cfg))
     if st != DROT_OK:

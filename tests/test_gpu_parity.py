@@ -79,11 +79,29 @@ def test_step_parity_small_and_ragged(solver, m, n, k):
     _step_parity(solver, pr, k, seed=m + n + k)
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("tile_k", [1, 2, 4])
-def test_step_parity_every_tile_width(tile_k):
+@pytest.mark.parametrize("grid", [37, 0])
+def test_step_parity_every_variant_and_tile_width(variant, tile_k, grid):
     pr = workloads.make_problem("plain_256", seed=5, m=203, n=1337)
-    with drot.Solver(device=0, tile_k=tile_k, grid_ctas=37) as s:
+    with drot.Solver(device=0, tile_k=tile_k, grid_ctas=grid, step_variant=variant) as s:
         _step_parity(s, pr, 2, seed=9)
+        assert s.profile()["step_variant"] == variant and s.profile()["tile_k"] == tile_k
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_variants_agree_bitwise_on_a_solve(variant):
+    # the two fused-step variants perform the same FP32 operations in the same order
+    # per entry and write the same partials, so whole runs agree bit for bit
+    pr = workloads.make_problem("plain_8192x6144", seed=12, m=517, n=1029)
+    outs = {}
+    for v in (1, 2):
+        C, p, q, X, mu, nu = _gpu_inputs(pr)
+        with drot.Solver(device=0, step_variant=v, tile_k=2, grid_ctas=53) as s:
+            o = s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=300, X=X, mu=mu, nu=nu)
+        outs[v] = (X.cpu().numpy(), mu.cpu().numpy(), o["primal_obj"])
+    assert np.array_equal(outs[1][0], outs[2][0])
+    assert np.array_equal(outs[1][1], outs[2][1]) and outs[1][2] == outs[2][2]
 
 
 def test_step_parity_full_size_8192x6144(solver):
