@@ -222,7 +222,7 @@ def run_ours(args):
     nu = torch.zeros(n, dtype=torch.float64, device=dev)
 
     rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
-    solver = drot.Solver(device=local, profile=True, stop_rule=rule)
+    solver = drot.Solver(device=local, profile=True, stop_rule=rule, step_variant=args.step_variant)
 
     def one_solve():
         return solver.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
@@ -327,7 +327,8 @@ def run_ours(args):
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": "drot_step_kernel",
                      "step_ms": step_ms, "timed_launches": int(prof["step_launches"]),
                      "alg_bytes_per_launch": alg_bytes,
-                     "plan": {k: prof[k] for k in ("tile_k", "grid_ctas", "col_tiles", "graph_iters")}},
+                     "plan": {k: prof[k] for k in ("tile_k", "grid_ctas", "col_tiles", "graph_iters",
+                                                   "step_variant", "stages")}},
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -352,6 +353,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--stop", choices=["gap", "full"], default="gap")
+    ap.add_argument("--step-variant", type=int, default=0, choices=[0, 1, 2],
+                    help="fused step: 1 register-fed, 2 TMA-fed, 0 library default")
     ap.add_argument("--max-iter", type=int, default=3_000_000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample-iters", type=int, default=8)

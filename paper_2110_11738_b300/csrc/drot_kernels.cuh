@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
 // stores, and arrive on the stage's "empty" mbarrier.  Every wait is bounded:
 // after kWaitLimit polls the kernel records a fault in Scalars and returns.
 
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
