@@ -67,7 +67,8 @@ typedef enum {
     DROT_ERR_CUDA = 4,          /* a CUDA runtime call failed (message via drot_last_error) */
     DROT_NOT_CONVERGED = 5,     /* max_iter iterations ran; outputs hold the last iterate */
     DROT_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits */
-    DROT_ERR_NONFINITE = 7      /* a NaN/Inf appeared in the iteration; outputs hold the last iterate */
+    DROT_ERR_NONFINITE = 7,     /* a NaN/Inf appeared in the iteration; outputs hold the last iterate */
+    DROT_ERR_TOO_LARGE = 8      /* drot_solve_static: the problem's workspace exceeds DROT_STATIC_SCRATCH_BYTES */
 } drot_status;
 
 /* Quantities that gate the stopping test (bitmask, drot_config.stop_rule). */
@@ -152,6 +153,33 @@ drot_status drot_solve(drot_handle *h, int64_t m, int64_t n, const float *C, int
  * status among the problems (per-problem status in res[b].status). */
 drot_status drot_solve_batched(drot_handle *h, int32_t B, const drot_problem *probs, double tol,
                                int64_t max_iter, int warm, drot_result *res);
+
+/* Allocation-free solve.  The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate GPU memory at the time they solve - code that runs inside a memory pool or arena
+ * owned by another component (a framework's caching allocator, a renderer or a simulator that reserved
+ * all device memory at start-up), plugins whose host forbids cudaMalloc after initialisation, and
+ * latency-critical loops that must never enter the allocator.  Everyone else should use drot_solve.
+ *
+ * It solves one problem exactly like drot_solve with a default configuration (same arguments and
+ * meaning; rho <= 0 selects 2/(m+n); stop when gap <= tol and l1 residual <= tol), on device pointers
+ * of the caller's current device, without a handle.  It allocates nothing: no cudaMalloc or cudaFree,
+ * no pinned host memory, no CUDA graph.  Its workspace is one fixed array of
+ * DROT_STATIC_SCRATCH_BYTES (16 MiB) in the library's own device memory, which every GPU that loads
+ * the library keeps until the process exits.
+ *   - Size limit: the workspace is about 8*(3m + 2n + T*m) + 4096*(T + 2*SMs) + 8 KiB bytes with
+ *     T = ceil(n/512) (n >= 1536; narrower problems use narrower tiles).  m = n = 20000 fits (~8 MB).
+ *     A problem that does not fit returns DROT_ERR_TOO_LARGE before anything is launched.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ *     device current).  Make that first call before any stream capture is started on the device.
+ *   - Every call uses the same array.  Calls whose GPU work overlaps (other streams, other host
+ *     threads) race on it and corrupt each other's results: serialise them.  Each call initialises
+ *     every part of the array it reads, so nothing from an earlier call leaks into a later one.
+ *   - Work is issued on `stream` (a cudaStream_t; NULL: the default stream) and the call returns
+ *     after synchronising it, with X, mu, nu and *res (may be NULL) complete. */
+#define DROT_STATIC_SCRATCH_BYTES (16u << 20)
+drot_status drot_solve_static(int64_t m, int64_t n, const float *C, int64_t ld, const double *p,
+                              const double *q, double rho, double tol, int64_t max_iter, float *X,
+                              double *mu, double *nu, int warm, void *stream, drot_result *res);
 
 /* Release the handle and its workspace (NULL is accepted). */
 drot_status drot_destroy(drot_handle *h);

@@ -15,6 +15,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -720,6 +721,7 @@ const char *drot_status_string(drot_status s) {
         case DROT_NOT_CONVERGED: return "iteration cap reached";
         case DROT_ERR_TIMEOUT: return "device wait timed out";
         case DROT_ERR_NONFINITE: return "non-finite value in the iteration";
+        case DROT_ERR_TOO_LARGE: return "problem too large for the static workspace of drot_solve_static";
     }
     return "unknown status";
 }
@@ -727,3 +729,225 @@ const char *drot_status_string(drot_status s) {
 const char *drot_last_error(drot_handle *h) { return h ? h->last_error.c_str() : ""; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free entry point (drot_solve_static).  For callers that may not allocate
+// device memory when they solve; see include/drot.h.  The workspace is the file-scope
+// array below; host code reaches it only through the address cudaGetSymbolAddress
+// returns for the current device (the array's name is not a device address on the host).
+
+static __device__ __align__(256) unsigned char drot_static_scratch[DROT_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+constexpr int kStaticMaxCtas = 512;
+constexpr int kStaticMaxTiles = 8192;
+
+std::mutex g_static_mu;       // guards the per-device address table
+std::mutex g_static_call_mu;  // serialises calls (they share the workspace and the host tables)
+void *g_static_addr[kStaticMaxDevices] = {};
+long long g_static_wbound[kStaticMaxCtas + 1];
+int g_static_slot_base[kStaticMaxCtas];
+int g_static_tile_slot[kStaticMaxTiles + 1];
+
+// Device address of the static workspace on `dev` (looked up once per device).
+cudaError_t static_workspace(int dev, void **out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, drot_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = ptr;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, int64_t ld, const double *p,
+                                         const double *q, double rho, double tol, int64_t max_iter, float *X,
+                                         double *mu, double *nu, int warm, void *stream_ptr, drot_result *res) {
+    const auto t_start = std::chrono::steady_clock::now();
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    if (m < 1 || n < 1 || ld < n || ld % 4 != 0 || max_iter < 0 || std::isnan(tol)) return DROT_ERR_INVALID_ARG;
+    if (!C || !p || !q || !X || !mu || !nu) return DROT_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15) return DROT_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(mu) |
+         reinterpret_cast<uintptr_t>(nu)) & 7)
+        return DROT_ERR_INVALID_ARG;
+    if (m > (1LL << 40) / n) return DROT_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return DROT_ERR_CUDA;
+    const void *ptrs[6] = {C, p, q, X, mu, nu};
+    for (const void *ptr : ptrs)
+        if (!is_device_ptr(ptr, dev)) return DROT_ERR_INVALID_ARG;
+    if (!(rho > 0.0)) rho = 2.0 / (double)(m + n);
+    if (!std::isfinite(rho)) return DROT_ERR_INVALID_ARG;
+    int num_sms = 148;
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+
+    // launch plan: register-fed fused step, tables in fixed-size host arrays
+    const int K = n >= 1536 ? 4 : (n >= 384 ? 2 : 1);
+    const int TW = 128 * K;
+    const long long T = (n + TW - 1) / TW;
+    if (T > kStaticMaxTiles) return DROT_ERR_TOO_LARGE;
+    const long long units = T * m;
+    const int G = (int)std::min<long long>(
+        std::min<long long>(2LL * num_sms, kStaticMaxCtas),
+        std::max<long long>(1, (units + drot::kWarps - 1) / drot::kWarps));
+    std::lock_guard<std::mutex> call_lock(g_static_call_mu);
+    long long *wbound = g_static_wbound;
+    int *slot_base = g_static_slot_base;
+    int *tile_slot = g_static_tile_slot;
+    const long long last_w = n - (T - 1) * TW;
+    const double full_cost = (double)((T - 1) * m) * TW;
+    const double total_cost = full_cost + (double)m * last_w;
+    wbound[0] = 0;
+    for (int g = 1; g < G; ++g) {
+        const double cost = total_cost * g / G;
+        long long u = cost <= full_cost ? (long long)std::llround(cost / TW)
+                                        : (T - 1) * m + (long long)std::llround((cost - full_cost) / (double)last_w);
+        u = std::min(std::max<long long>(u, 0), units);
+        wbound[g] = std::max(wbound[g - 1], u);
+    }
+    wbound[G] = units;
+    int slots = 0;
+    for (long long t = 0; t <= T; ++t) tile_slot[t] = -1;
+    for (int g = 0; g < G; ++g) {
+        slot_base[g] = slots;
+        if (wbound[g + 1] <= wbound[g]) continue;
+        for (long long t = wbound[g] / m; t <= (wbound[g + 1] - 1) / m; ++t) {
+            if (tile_slot[t] < 0) tile_slot[t] = slots;
+            ++slots;
+        }
+    }
+    tile_slot[T] = slots;
+    for (long long t = T - 1; t >= 0; --t)
+        if (tile_slot[t] < 0) tile_slot[t] = tile_slot[t + 1];
+    const int fin_blocks = (int)std::min<long long>(2LL * num_sms, std::max<long long>(1, (m + n + 255) / 256));
+
+    // workspace layout inside the static array
+    const size_t need = align_up(sizeof(Scalars), 256) + align_up(sizeof(double) * m, 256) * 2 +
+                        align_up(sizeof(double) * n, 256) * 2 + align_up(sizeof(double) * (size_t)T * m, 256) +
+                        align_up(sizeof(double) * (size_t)std::max(slots, 1) * TW, 256) +
+                        align_up(sizeof(double) * 2 * G, 256) +
+                        align_up(sizeof(double) * drot::kFinishAcc * fin_blocks, 256) +
+                        align_up(sizeof(long long) * (G + 1), 256) + align_up(sizeof(int) * G, 256) +
+                        align_up(sizeof(int) * (T + 1), 256);
+    if (need > (size_t)DROT_STATIC_SCRATCH_BYTES) return DROT_ERR_TOO_LARGE;
+    void *base = nullptr;
+    if (static_workspace(dev, &base) != cudaSuccess) return DROT_ERR_CUDA;
+    char *cur = static_cast<char *>(base);
+    Scalars *sc = carve<Scalars>(cur, 1);
+    double *g_num = carve<double>(cur, m), *a_vec = carve<double>(cur, m);
+    double *h_num = carve<double>(cur, n), *b_vec = carve<double>(cur, n);
+    double *rowpart = carve<double>(cur, (size_t)T * m);
+    double *colpart = carve<double>(cur, (size_t)std::max(slots, 1) * TW);
+    double *ctapart = carve<double>(cur, 2 * (size_t)G);
+    double *finpart = carve<double>(cur, (size_t)drot::kFinishAcc * fin_blocks);
+    long long *d_wbound = carve<long long>(cur, G + 1);
+    int *d_slot_base = carve<int>(cur, G);
+    int *d_tile_slot = carve<int>(cur, T + 1);
+
+#define STATIC_CUDA(call)                                  \
+    do {                                                   \
+        if ((call) != cudaSuccess) return DROT_ERR_CUDA;   \
+    } while (0)
+
+    STATIC_CUDA(cudaMemcpyAsync(d_wbound, wbound, sizeof(long long) * (G + 1), cudaMemcpyHostToDevice, stream));
+    STATIC_CUDA(cudaMemcpyAsync(d_slot_base, slot_base, sizeof(int) * G, cudaMemcpyHostToDevice, stream));
+    STATIC_CUDA(cudaMemcpyAsync(d_tile_slot, tile_slot, sizeof(int) * (T + 1), cudaMemcpyHostToDevice, stream));
+    Scalars init{};
+    init.rho = rho;
+    init.tol = tol;
+    init.max_iter = max_iter;
+    init.stop_rule = DROT_STOP_GAP | DROT_STOP_RES_L1;
+    init.done = drot::kRunning;
+    STATIC_CUDA(cudaMemcpyAsync(sc, &init, sizeof init, cudaMemcpyHostToDevice, stream));
+    drot::drot_vector_sums_kernel<<<1, 1024, 0, stream>>>(p, q, warm ? mu : nullptr, warm ? nu : nullptr, m, n, sc);
+    STATIC_CUDA(cudaGetLastError());
+    Scalars st{};
+    STATIC_CUDA(cudaMemcpyAsync(&st, sc, sizeof st, cudaMemcpyDeviceToHost, stream));
+    STATIC_CUDA(cudaStreamSynchronize(stream));
+    if (st.nonfinite_input & 3) return DROT_ERR_MARGINALS;
+    if (st.nonfinite_input & 4) return DROT_ERR_INVALID_ARG;
+    if (!(std::fabs(st.sum_p - st.sum_q) <= 1e-9 * std::max(1.0, std::fabs(st.sum_p)))) return DROT_ERR_MARGINALS;
+
+    Plan P;
+    P.K = K;
+    P.TW = TW;
+    P.T = (int)T;
+    P.G = G;
+    P.slots = std::max(slots, 1);
+    P.fin_blocks = fin_blocks;
+    P.variant = 1;
+    drot::StepArgs A{};
+    A.C = C; A.X = X; A.g = g_num; A.h = h_num; A.sc = sc;
+    A.rowpart = rowpart; A.colpart = colpart; A.ctapart = ctapart;
+    A.wbound = d_wbound; A.slot_base = d_slot_base;
+    A.m = m; A.n = n; A.ld = ld; A.inv_n = 1.0 / (double)n; A.inv_m = 1.0 / (double)m;
+    drot::FinishArgs F{};
+    F.rowpart = rowpart; F.colpart = colpart; F.ctapart = ctapart; F.tile_slot = d_tile_slot;
+    F.p = p; F.q = q; F.a = a_vec; F.b = b_vec; F.g = g_num; F.h = h_num; F.finpart = finpart; F.sc = sc;
+    F.m = m; F.n = n; F.T = (int)T; F.TW = TW; F.G = G; F.inv_n = 1.0 / (double)n; F.inv_m = 1.0 / (double)m;
+
+    if (!warm) {
+        const long long work = m * ((n + 3) / 4);
+        const int blocks = (int)std::min<long long>(8LL * num_sms, std::max<long long>(1, (work + 255) / 256));
+        drot::drot_init_plan_kernel<<<blocks, 256, 0, stream>>>(X, p, q, m, n, ld);
+        STATIC_CUDA(cudaGetLastError());
+    }
+    STATIC_CUDA(launch_step<false>(P, A, stream));
+    drot::drot_init_state_kernel<<<fin_blocks, drot::kFinishThreads, 0, stream>>>(F, warm ? mu : nullptr,
+                                                                                 warm ? nu : nullptr);
+    STATIC_CUDA(cudaGetLastError());
+
+    int done = max_iter > 0 ? drot::kRunning : drot::kIterCap;
+    if (max_iter > 0) {
+        const double t_iter = 12.0 * (double)m * (double)n / 6.0e12 + 6.0e-6;
+        const long long chunk = std::max(1L, std::min(256L, std::lround(2.0e-3 / t_iter)));
+        const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
+        for (long long c = 0; c < max_chunks && done == drot::kRunning; ++c) {
+            for (long long it = 0; it < chunk; ++it) {
+                STATIC_CUDA(launch_step<true>(P, A, stream));
+                drot::drot_finish_kernel<<<fin_blocks, drot::kFinishThreads, 0, stream>>>(F);
+                STATIC_CUDA(cudaGetLastError());
+            }
+            STATIC_CUDA(cudaMemcpyAsync(&st, sc, sizeof st, cudaMemcpyDeviceToHost, stream));
+            STATIC_CUDA(cudaStreamSynchronize(stream));
+            done = st.done;
+        }
+        if (done == drot::kRunning) return DROT_ERR_CUDA;
+    }
+    const int eblocks = (int)std::min<long long>(2LL * num_sms, std::max<long long>(1, (m + n + 255) / 256));
+    drot::drot_export_duals_kernel<<<eblocks, 256, 0, stream>>>(g_num, h_num, sc, mu, nu, m, n, 1.0 / n, 1.0 / m);
+    STATIC_CUDA(cudaGetLastError());
+    STATIC_CUDA(cudaMemsetAsync(&sc->nnz, 0, sizeof(unsigned long long), stream));
+    const int nblocks = (int)std::min<long long>(8LL * num_sms, std::max<long long>(1, (m * n + 255) / 256));
+    drot::drot_count_nnz_kernel<<<nblocks, 256, 0, stream>>>(X, m, n, ld, sc);
+    STATIC_CUDA(cudaGetLastError());
+    STATIC_CUDA(cudaMemcpyAsync(&st, sc, sizeof st, cudaMemcpyDeviceToHost, stream));
+    STATIC_CUDA(cudaStreamSynchronize(stream));
+#undef STATIC_CUDA
+
+    drot_status out = DROT_OK;
+    if (done == drot::kIterCap) out = DROT_NOT_CONVERGED;
+    else if (done == drot::kNonFinite) out = DROT_ERR_NONFINITE;
+    else if (done == drot::kFault) out = DROT_ERR_TIMEOUT;
+    if (res) {
+        res->iters = st.k;
+        res->primal_obj = st.primal;
+        res->dual_obj = st.dual;
+        res->gap = st.gap;
+        res->res_l1 = st.res_l1;
+        res->res_l2 = st.res_l2;
+        res->dual_res = st.dual_res_prev;
+        res->nnz = (int64_t)st.nnz;
+        res->status = out;
+        if (st.k == 0) res->primal_obj = res->dual_obj = res->gap = res->res_l1 = res->res_l2 = res->dual_res = NAN;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    return out;
+}

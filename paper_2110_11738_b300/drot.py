@@ -28,16 +28,19 @@ DROT_ERR_CUDA = 4
 DROT_NOT_CONVERGED = 5
 DROT_ERR_TIMEOUT = 6
 DROT_ERR_NONFINITE = 7
+DROT_ERR_TOO_LARGE = 8
 
 STATUS_NAMES = {
     DROT_OK: "DROT_OK", DROT_ERR_INVALID_ARG: "DROT_ERR_INVALID_ARG", DROT_ERR_MARGINALS: "DROT_ERR_MARGINALS",
     DROT_ERR_OOM: "DROT_ERR_OOM", DROT_ERR_CUDA: "DROT_ERR_CUDA", DROT_NOT_CONVERGED: "DROT_NOT_CONVERGED",
     DROT_ERR_TIMEOUT: "DROT_ERR_TIMEOUT", DROT_ERR_NONFINITE: "DROT_ERR_NONFINITE",
+    DROT_ERR_TOO_LARGE: "DROT_ERR_TOO_LARGE",
 }
 
 # Every symbol include/drot.h declares.
 EXPORTED = ("drot_config_default", "drot_create", "drot_solve", "drot_solve_batched", "drot_destroy",
-            "drot_get_profile", "drot_reset_profile", "drot_status_string", "drot_last_error")
+            "drot_get_profile", "drot_reset_profile", "drot_status_string", "drot_last_error",
+            "drot_solve_static")
 
 
 class DrotConfig(ctypes.Structure):
@@ -112,6 +115,9 @@ def load(build_if_missing: bool = True):
     lib.drot_status_string.argtypes = [ctypes.c_int]
     lib.drot_last_error.restype = ctypes.c_char_p
     lib.drot_last_error.argtypes = [vp]
+    lib.drot_solve_static.restype = ctypes.c_int
+    lib.drot_solve_static.argtypes = [i64, i64, vp, i64, vp, vp, ctypes.c_double, ctypes.c_double, i64, vp, vp, vp,
+                                      ctypes.c_int, vp, ctypes.POINTER(DrotResult)]
     _lib = lib
     return lib
 
@@ -221,6 +227,32 @@ def drot_solve_batched(handle: int, problems: Sequence[dict], tol: float = 1e-6,
     if check and st not in (DROT_OK, DROT_NOT_CONVERGED):
         raise DrotError(st, lib.drot_last_error(ctypes.c_void_p(handle)).decode())
     return [_result_dict(res[b]) for b in range(B)]
+
+
+def drot_solve_static(C, p, q, rho: float = 0.0, tol: float = 1e-6, max_iter: int = 1_000_000, X=None, mu=None,
+                      nu=None, warm: bool = False, n: Optional[int] = None, stream: Optional[int] = None) -> dict:
+    """Call drot_solve_static: the handle-free solve that allocates no device memory.
+
+    For callers that cannot allocate GPU memory when they solve (see include/drot.h).  All
+    buffers must be CUDA tensors on the current device; X, mu, nu are written in place.
+    Returns the result dict; "status" holds the drot_status (DROT_ERR_TOO_LARGE when the
+    problem does not fit the library's fixed 16 MiB workspace).
+    """
+    lib = load()
+    m = int(C.shape[0])
+    n = int(C.shape[1]) if n is None else int(n)
+    ld = _ld_of(C)
+    if X is not None and _ld_of(X) != ld:
+        raise ValueError("C and X must share the row pitch")
+    res = DrotResult()
+    st = lib.drot_solve_static(m, n, ctypes.c_void_p(_ptr(C)), ld, ctypes.c_void_p(_ptr(p)),
+                               ctypes.c_void_p(_ptr(q)), float(rho), float(tol), int(max_iter),
+                               ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(mu)), ctypes.c_void_p(_ptr(nu)),
+                               int(bool(warm)), ctypes.c_void_p(stream or 0), ctypes.byref(res))
+    out = _result_dict(res)
+    out["status"] = int(st)
+    out["status_name"] = STATUS_NAMES.get(int(st), str(st))
+    return out
 
 
 def drot_get_profile(handle: int) -> dict:
