@@ -222,7 +222,8 @@ def run_ours(args):
     nu = torch.zeros(n, dtype=torch.float64, device=dev)
 
     rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
-    solver = drot.Solver(device=local, profile=True, stop_rule=rule, step_variant=args.step_variant)
+    solver = drot.Solver(device=local, profile=True, stop_rule=rule, step_variant=args.step_variant,
+                         autotune=not args.no_autotune, deterministic=args.deterministic)
 
     def one_solve():
         return solver.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
@@ -318,7 +319,9 @@ def run_ours(args):
         "config": {"workload": args.workload, "m": m, "n": n, "ld": ld, "seed": args.seed, "tol": args.tol,
                    "rho": pr.rho, "stop_rule": {"gap": "gap<=tol", "full": "gap<=tol and l1 residual<=tol"}[args.stop],
                    "l2": f"inputs larger than L2 (C+X = {2 * m * ld * 4 / 1e6:.0f} MB > 126 MB)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "sums": "fixed-order partials" if args.deterministic else "FP64 atomics",
+                   "plan": "autotuned" if not args.no_autotune else "default"},
         "iters_to_tol": iters,
         "status": statuses,
         "ms_per_iter": ms_per_solve / statistics.mean(iters),
@@ -326,6 +329,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": "drot_step_kernel",
                      "step_ms": step_ms, "timed_launches": int(prof["step_launches"]),
+                     "finish_ms": prof["finish_ms_total"] / max(1, prof["step_launches"]),
+                     "step_plus_finish_ms": prof["iter_ms_total"] / max(1, prof["step_launches"]),
                      "alg_bytes_per_launch": alg_bytes,
                      "plan": {k: prof[k] for k in ("tile_k", "grid_ctas", "col_tiles", "graph_iters",
                                                    "step_variant", "stages")}},
@@ -353,6 +358,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--stop", choices=["gap", "full"], default="gap")
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's default plan")
+    ap.add_argument("--deterministic", action="store_true", help="fixed-order partial sums instead of atomics")
     ap.add_argument("--step-variant", type=int, default=0, choices=[0, 1, 2],
                     help="fused step: 1 register-fed, 2 TMA-fed, 0 library default")
     ap.add_argument("--max-iter", type=int, default=3_000_000)

@@ -87,6 +87,12 @@ typedef struct {
     int profile;                /* 1: time every fused-step launch with CUDA events (drot_get_profile) */
     int step_variant;           /* fused step: 1 register-fed (128-bit loads), 2 TMA-fed (bulk copies into a
                                    shared-memory ring); 0: automatic */
+    int deterministic;          /* 1: row/column sums as fixed-order FP64 partials (bitwise reproducible
+                                   runs); 0 (default): FP64 atomic adds into the totals (faster; the
+                                   summation order, hence the last bits, may vary between runs) */
+    int autotune;               /* 1: on the first solve of each (m, n), time the fused-step variants and tile
+                                   widths on a scratch plan and keep the fastest (costs one m x ld FP32
+                                   scratch buffer and a few launches); explicit step_variant / tile_k win */
 } drot_config;
 
 typedef struct {
@@ -119,6 +125,8 @@ typedef struct {
     int64_t graph_replays;      /* CUDA-graph replays issued */
     int32_t tile_k, grid_ctas, col_tiles, graph_iters;  /* the plan of the last solve */
     int32_t step_variant, stages;                       /* fused-step variant and ring depth used */
+    double finish_ms_total;     /* summed device time of the finish launches of the timed iterations */
+    double iter_ms_total;       /* summed device time from each timed step launch to the next one */
 } drot_profile;
 
 /* Fill cfg with the defaults listed above. */

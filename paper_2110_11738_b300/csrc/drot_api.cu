@@ -21,6 +21,7 @@
 
 #include "../../include/drot.h"
 #include "drot_kernels.cuh"
+#include "drot_batched.cuh"
 
 using drot::Scalars;
 
@@ -29,6 +30,7 @@ namespace {
 struct Plan {
     int K = 4, TW = 512, T = 1, G = 1, slots = 1, fin_blocks = 1, graph_iters = 1;
     int variant = 1, S = 0;  // fused-step variant (1 register-fed, 2 TMA-fed) and ring stages
+    int accumulate = 1;      // 1: FP64 atomics into row/column totals; 0: fixed-order partials
     std::vector<long long> wbound;  // G+1
     std::vector<int> slot_base;     // G
     std::vector<int> tile_slot;     // T+1
@@ -38,11 +40,11 @@ struct GraphKey {
     long long m = -1, n = -1, ld = -1;
     const void *C = nullptr, *X = nullptr, *p = nullptr, *q = nullptr;
     const void *arena = nullptr;
-    int K = 0, G = 0, graph_iters = 0, profile = 0, variant = 0;
+    int K = 0, G = 0, graph_iters = 0, profile = 0, variant = 0, accumulate = 0;
     bool operator==(const GraphKey &o) const {
         return m == o.m && n == o.n && ld == o.ld && C == o.C && X == o.X && p == o.p && q == o.q &&
                arena == o.arena && K == o.K && G == o.G && graph_iters == o.graph_iters && profile == o.profile &&
-               variant == o.variant;
+               variant == o.variant && accumulate == o.accumulate;
     }
 };
 
@@ -54,7 +56,8 @@ struct Arena {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Ring depth of the TMA-fed step for a tile width (each stage holds 8 rows of X and C).
-int tma_stages(int K) { return K == 4 ? 4 : (K == 2 ? 8 : 16); }
+// K = 4 rings take 160 KB (one CTA per SM); K = 2 and K = 1 rings fit two CTAs per SM.
+int tma_stages(int K) { return K == 4 ? 4 : (K == 2 ? 4 : 8); }
 
 template <int K, int S>
 cudaError_t set_tma_attr() {
@@ -65,10 +68,28 @@ cudaError_t set_tma_attr() {
 // Opt the TMA-fed kernels into their shared-memory ring size on the current device
 // (done once per handle, outside any stream capture).
 cudaError_t set_kernel_attributes() {
-    cudaError_t e = set_tma_attr<1, 16>();
-    if (e == cudaSuccess) e = set_tma_attr<2, 8>();
+    cudaError_t e = set_tma_attr<1, 8>();
+    if (e == cudaSuccess) e = set_tma_attr<2, 4>();
     if (e == cudaSuccess) e = set_tma_attr<4, 4>();
     return e;
+}
+
+template <int K, int S>
+int tma_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, drot::drot_step_tma_kernel<K, S>, drot::kThreads + 32,
+                                                      drot::TmaLayout<K, S>::bytes) != cudaSuccess)
+        return -1;
+    return nb;
+}
+
+template <int K>
+int ldg_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, drot::drot_step_kernel<K, true>, drot::kThreads, 0) !=
+        cudaSuccess)
+        return -1;
+    return nb;
 }
 
 template <int K, int S>
@@ -100,12 +121,43 @@ struct drot_handle {
     // per-solve carved pointers
     double *g = nullptr, *h = nullptr, *a = nullptr, *b = nullptr;
     double *rowpart = nullptr, *colpart = nullptr, *ctapart = nullptr, *finpart = nullptr;
+    double *u = nullptr, *v = nullptr, *acc = nullptr;
     long long *wbound = nullptr;
     int *slot_base = nullptr, *tile_slot = nullptr;
 
     drot_profile prof{};
     std::string last_error;
+
+    int occ[3][5] = {};  // resident CTAs per SM of the fused step [variant][K]
+    struct Tuned {
+        long long m, n;
+        int variant, K;
+    };
+    std::vector<Tuned> tuned;  // autotuner choices per problem shape
+    Arena tune_x;              // scratch plan the autotuner streams over
+
+    // batched solver state
+    Arena batch;                        // per-problem vectors, scalars and work lists
+    Scalars *h_bstat = nullptr;         // pinned read-back of every problem's scalars
+    size_t h_bstat_cap = 0;
+    cudaGraphExec_t bexec = nullptr;
+    int batch_k_thresholds[2] = {0, 0};  // autotuned tile policy: K = 1 below t0, 2 below t1, else 4
 };
+
+namespace {
+cudaError_t fill_occupancy(drot_handle *h) {
+    const int v[3][5] = {{0, 0, 0, 0, 0},
+                         {0, ldg_occupancy<1>(), ldg_occupancy<2>(), 0, ldg_occupancy<4>()},
+                         {0, tma_occupancy<1, 8>(), tma_occupancy<2, 4>(), 0, tma_occupancy<4, 4>()}};
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 5; ++k) {
+            if (v[a][k] < 0) return cudaErrorUnknown;
+            h->occ[a][k] = v[a][k];
+        }
+    return cudaSuccess;
+}
+
+}  // namespace
 
 namespace {
 
@@ -157,8 +209,16 @@ bool is_device_ptr(const void *p, int device) {
 // ranges are balanced by the number of columns they cover (a ragged last tile
 // costs less per row), and slots are numbered in CTA order, which is also
 // column-tile order.
-void make_plan(const drot_handle *h, long long m, long long n, Plan &P) {
-    int K = h->cfg.tile_k;
+void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int force_variant = 0, int force_k = 0) {
+    int K = force_k ? force_k : h->cfg.tile_k;
+    int variant = force_variant ? force_variant : h->cfg.step_variant;
+    if (!force_k && !force_variant && h->cfg.autotune) {
+        for (const auto &t : h->tuned)
+            if (t.m == m && t.n == n) {
+                if (K != 1 && K != 2 && K != 4) K = t.K;
+                if (variant != 1 && variant != 2) variant = t.variant;
+            }
+    }
     if (K != 1 && K != 2 && K != 4) {
         if (n >= 1536) K = 4;
         else if (n >= 384) K = 2;
@@ -168,16 +228,16 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P) {
     P.TW = 128 * K;
     P.T = (int)((n + P.TW - 1) / P.TW);
     const long long units = (long long)P.T * m;
-    int variant = h->cfg.step_variant;
     if (variant != 1 && variant != 2) variant = 1;
     P.variant = variant;
     P.S = variant == 2 ? tma_stages(K) : 0;
+    P.accumulate = h->cfg.deterministic ? 0 : 1;
     int G = h->cfg.grid_ctas;
     if (G <= 0) {
-        // register-fed: two resident CTAs per SM; TMA-fed: one CTA (and one ring) per SM.
-        // Small problems use fewer CTAs so that each warp has rows.
+        // as many CTAs as fit on the SMs at once (one wave); small problems use fewer
+        // CTAs so that each warp has rows
         const long long want = (units + drot::kWarps - 1) / drot::kWarps;
-        const long long per_sm = variant == 2 ? 1 : 2;
+        const long long per_sm = std::max(1, h->occ[variant][K]);
         G = (int)std::min<long long>(per_sm * h->num_sms, std::max<long long>(1, want));
     }
     G = (int)std::min<long long>(G, std::max<long long>(1, units));
@@ -239,7 +299,8 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
                          align_up(sizeof(double) * 2 * P.G, 256) +
                          align_up(sizeof(double) * drot::kFinishAcc * P.fin_blocks, 256) +
                          align_up(sizeof(long long) * (P.G + 1), 256) + align_up(sizeof(int) * P.G, 256) +
-                         align_up(sizeof(int) * (P.T + 1), 256) + 4096;
+                         align_up(sizeof(int) * (P.T + 1), 256) + align_up(sizeof(double) * m, 256) +
+                         align_up(sizeof(double) * n, 256) + 256 + 4096;
     drot_status st = arena_reserve(h, h->work, bytes);
     if (st != DROT_OK) return st;
     char *cur = static_cast<char *>(h->work.ptr);
@@ -255,6 +316,15 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
     h->wbound = carve<long long>(cur, P.G + 1);
     h->slot_base = carve<int>(cur, P.G);
     h->tile_slot = carve<int>(cur, P.T + 1);
+    h->u = carve<double>(cur, m);
+    h->v = carve<double>(cur, n);
+    h->acc = carve<double>(cur, 2);
+    if (P.accumulate) {
+        // totals start at zero; every finish pass resets what it reads
+        DROT_CUDA(h, cudaMemsetAsync(h->u, 0, sizeof(double) * m, h->stream));
+        DROT_CUDA(h, cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream));
+        DROT_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * 2, h->stream));
+    }
     DROT_CUDA(h, cudaMemcpyAsync(h->wbound, P.wbound.data(), sizeof(long long) * (P.G + 1), cudaMemcpyHostToDevice,
                                  h->stream));
     DROT_CUDA(h, cudaMemcpyAsync(h->slot_base, P.slot_base.data(), sizeof(int) * P.G, cudaMemcpyHostToDevice,
@@ -264,8 +334,13 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
     return DROT_OK;
 }
 
-drot::StepArgs step_args(const drot_handle *h, long long m, long long n, long long ld, const float *C, float *X) {
+drot::StepArgs step_args(const drot_handle *h, const Plan &P, long long m, long long n, long long ld, const float *C,
+                         float *X) {
     drot::StepArgs A{};
+    A.u = h->u;
+    A.v = h->v;
+    A.acc = h->acc;
+    A.accumulate = P.accumulate;
     A.C = C;
     A.X = X;
     A.g = h->g;
@@ -287,6 +362,10 @@ drot::StepArgs step_args(const drot_handle *h, long long m, long long n, long lo
 drot::FinishArgs finish_args(const drot_handle *h, long long m, long long n, const Plan &P, const double *p,
                              const double *q) {
     drot::FinishArgs F{};
+    F.u = h->u;
+    F.v = h->v;
+    F.acc = h->acc;
+    F.accumulate = P.accumulate;
     F.rowpart = h->rowpart;
     F.colpart = h->colpart;
     F.ctapart = h->ctapart;
@@ -313,8 +392,8 @@ template <bool UPDATE>
 cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s) {
     if (UPDATE && P.variant == 2) {
         switch (P.K) {
-            case 1: return launch_tma<1, 16>(P.G, A, s);
-            case 2: return launch_tma<2, 8>(P.G, A, s);
+            case 1: return launch_tma<1, 8>(P.G, A, s);
+            case 2: return launch_tma<2, 4>(P.G, A, s);
             default: return launch_tma<4, 4>(P.G, A, s);
         }
     }
@@ -343,21 +422,25 @@ drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, con
     const bool prof = key.profile != 0;
     for (int inst = 0; inst < 2; ++inst) {
         if (prof) {
-            h->ev[inst].resize(2 * P.graph_iters);
+            h->ev[inst].resize(3 * P.graph_iters + 1);
             for (auto &e : h->ev[inst]) DROT_CUDA(h, cudaEventCreate(&e));
         }
         cudaGraph_t graph = nullptr;
         DROT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t err = cudaSuccess;
+        // profile events per iteration: [3 it] before the step, [3 it + 1] between step and
+        // finish, [3 it + 2] after the finish; [3 G] closes the last iteration
         for (int it = 0; it < P.graph_iters && err == cudaSuccess; ++it) {
-            if (prof) err = cudaEventRecordWithFlags(h->ev[inst][2 * it], h->stream, cudaEventRecordExternal);
+            if (prof) err = cudaEventRecordWithFlags(h->ev[inst][3 * it], h->stream, cudaEventRecordExternal);
             if (err == cudaSuccess) err = launch_step<true>(P, A, h->stream);
             if (prof && err == cudaSuccess)
-                err = cudaEventRecordWithFlags(h->ev[inst][2 * it + 1], h->stream, cudaEventRecordExternal);
+                err = cudaEventRecordWithFlags(h->ev[inst][3 * it + 1], h->stream, cudaEventRecordExternal);
             if (err == cudaSuccess) {
                 drot::drot_finish_kernel<<<P.fin_blocks, drot::kFinishThreads, 0, h->stream>>>(F);
                 err = cudaGetLastError();
             }
+            if (prof && err == cudaSuccess)
+                err = cudaEventRecordWithFlags(h->ev[inst][3 * it + 2], h->stream, cudaEventRecordExternal);
         }
         cudaError_t end = cudaStreamEndCapture(h->stream, &graph);
         if (err != cudaSuccess || end != cudaSuccess) {
@@ -373,15 +456,61 @@ drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, con
     return DROT_OK;
 }
 
+// Time every fused-step plan candidate (variant x tile width) for this shape on a
+// scratch plan, three launches each after one warm-up, and keep the fastest.
+// Runs after the scalar state is uploaded (the kernels read rho and the done flag);
+// the real plan's set-up afterwards re-zeroes every total the candidates touched.
+drot_status autotune_shape(drot_handle *h, long long m, long long n, long long ld, const float *C) {
+    for (const auto &t : h->tuned)
+        if (t.m == m && t.n == n) return DROT_OK;
+    const size_t bytes = sizeof(float) * (size_t)m * ld;
+    drot_status st = arena_reserve(h, h->tune_x, bytes);
+    if (st != DROT_OK) return st;
+    float *Xs = static_cast<float *>(h->tune_x.ptr);
+    DROT_CUDA(h, cudaMemsetAsync(Xs, 0, bytes, h->stream));
+    cudaEvent_t e0, e1;
+    DROT_CUDA(h, cudaEventCreate(&e0));
+    DROT_CUDA(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = 1, best_k = 1;
+    drot_status out = DROT_OK;
+    for (int variant = 1; variant <= 2 && out == DROT_OK; ++variant) {
+        for (int K : {1, 2, 4}) {
+            if (K > 1 && n < 64LL * K) continue;  // a tile more than twice the row width leaves most lanes idle
+            Plan P;
+            make_plan(h, m, n, P, variant, K);
+            out = setup_workspace(h, m, n, P);
+            if (out != DROT_OK) break;
+            DROT_CUDA(h, cudaMemsetAsync(h->g, 0, sizeof(double) * m, h->stream));
+            DROT_CUDA(h, cudaMemsetAsync(h->h, 0, sizeof(double) * n, h->stream));
+            const drot::StepArgs A = step_args(h, P, m, n, ld, C, Xs);
+            DROT_CUDA(h, launch_step<true>(P, A, h->stream));
+            DROT_CUDA(h, cudaEventRecord(e0, h->stream));
+            for (int r = 0; r < 3; ++r) DROT_CUDA(h, launch_step<true>(P, A, h->stream));
+            DROT_CUDA(h, cudaEventRecord(e1, h->stream));
+            DROT_CUDA(h, cudaEventSynchronize(e1));
+            h->prof.kernel_launches += 4;
+            float ms = 0.f;
+            DROT_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_v = variant;
+                best_k = K;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out != DROT_OK) return out;
+    h->tuned.push_back({m, n, best_v, best_k});
+    return DROT_OK;
+}
+
 // The solve on device pointers.
 drot_status solve_device(drot_handle *h, long long m, long long n, const float *C, long long ld, const double *p,
                          const double *q, double rho, double tol, long long max_iter, float *X, double *mu,
                          double *nu, int warm, drot_result *res) {
-    Plan P;
-    make_plan(h, m, n, P);
-    drot_status st = setup_workspace(h, m, n, P);
-    if (st != DROT_OK) return st;
-
+    drot_status st = DROT_OK;
     // scalar state; marginal sums and the warm duals' sums first
     Scalars &S = *h->h_sc;
     std::memset(&S, 0, sizeof S);
@@ -404,6 +533,15 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     if (!(std::fabs(chk.sum_p - chk.sum_q) <= 1e-9 * std::max(1.0, std::fabs(chk.sum_p))))
         return fail(h, DROT_ERR_MARGINALS, "sum(p) = %.17g and sum(q) = %.17g differ", chk.sum_p, chk.sum_q);
 
+    if (h->cfg.autotune) {
+        st = autotune_shape(h, m, n, ld, C);
+        if (st != DROT_OK) return st;
+    }
+    Plan P;
+    make_plan(h, m, n, P);
+    st = setup_workspace(h, m, n, P);
+    if (st != DROT_OK) return st;
+
     // X_0 and the state derived from it
     if (!warm) {
         const long long work = m * ((n + 3) / 4);
@@ -412,7 +550,7 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
         DROT_CUDA(h, cudaGetLastError());
         h->prof.kernel_launches += 1;
     }
-    const drot::StepArgs A = step_args(h, m, n, ld, C, X);
+    const drot::StepArgs A = step_args(h, P, m, n, ld, C, X);
     const drot::FinishArgs F = finish_args(h, m, n, P, p, q);
     DROT_CUDA(h, launch_step<false>(P, A, h->stream));
     drot::drot_init_state_kernel<<<P.fin_blocks, drot::kFinishThreads, 0, h->stream>>>(F, warm ? mu : nullptr,
@@ -427,6 +565,7 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
         key.m = m; key.n = n; key.ld = ld; key.C = C; key.X = X; key.p = p; key.q = q;
         key.arena = h->work.ptr; key.K = P.K; key.G = P.G; key.graph_iters = P.graph_iters;
         key.variant = P.variant;
+        key.accumulate = P.accumulate;
         key.profile = h->cfg.profile ? 1 : 0;
         if (!(key == h->key) || !h->exec[0]) {
             st = build_graphs(h, key, P, A, F);
@@ -469,9 +608,13 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
             if (h->cfg.profile) {
                 const long long ran = s.k - k_prev;
                 for (long long it = 0; it < ran && it < P.graph_iters; ++it) {
-                    float ms = 0.f;
-                    if (cudaEventElapsedTime(&ms, h->ev[inst][2 * it], h->ev[inst][2 * it + 1]) == cudaSuccess) {
+                    float ms = 0.f, fms = 0.f, ims = 0.f;
+                    if (cudaEventElapsedTime(&ms, h->ev[inst][3 * it], h->ev[inst][3 * it + 1]) == cudaSuccess &&
+                        cudaEventElapsedTime(&fms, h->ev[inst][3 * it + 1], h->ev[inst][3 * it + 2]) == cudaSuccess &&
+                        cudaEventElapsedTime(&ims, h->ev[inst][3 * it], h->ev[inst][3 * it + 2]) == cudaSuccess) {
                         h->prof.step_ms_total += ms;
+                        h->prof.finish_ms_total += fms;
+                        h->prof.iter_ms_total += ims;
                         h->prof.step_launches += 1;
                     }
                 }
@@ -535,6 +678,320 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     return out;
 }
 
+
+// ------------------------------------------------------------------------------------
+// Batched solve (drot_solve_batched with device buffers).
+
+struct BatchLists {
+    std::vector<int> active;
+    std::vector<long long> unit0;   // nactive + 1
+    std::vector<long long> wbound;  // G + 1
+    std::vector<int> fin_prob, fin_local;  // FB
+};
+
+// Tile width policy: K = 1 for n < t0, 2 for n < t1, else 4.
+int batch_k(long long n, const int thr[2]) { return n < thr[0] ? 1 : (n < thr[1] ? 2 : 4); }
+
+// Segment list, byte-balanced CTA ranges and finish-block groups of the active problems.
+void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector<int> &active, int G, int FB,
+                       BatchLists &L) {
+    L.active = active;
+    const int na = (int)active.size();
+    L.unit0.assign(na + 1, 0);
+    std::vector<double> cost0(na + 1, 0.0);
+    for (int a = 0; a < na; ++a) {
+        const drot::BatchProb &P = hp[active[a]];
+        const long long TW = 128LL * P.K;
+        const long long units = (long long)P.T * P.m;
+        const long long last_w = P.n - (long long)(P.T - 1) * TW;
+        L.unit0[a + 1] = L.unit0[a] + units;
+        cost0[a + 1] = cost0[a] + (double)(P.T - 1) * P.m * TW + (double)P.m * last_w;
+    }
+    const long long total = L.unit0[na];
+    L.wbound.assign(G + 1, total);
+    L.wbound[0] = 0;
+    int a = 0;
+    for (int g = 1; g < G; ++g) {
+        const double target = cost0[na] * g / G;
+        while (a + 1 < na && cost0[a + 1] <= target) ++a;
+        long long u = total;
+        if (na > 0) {
+            const drot::BatchProb &P = hp[active[a]];
+            const long long TW = 128LL * P.K;
+            const long long last_w = P.n - (long long)(P.T - 1) * TW;
+            const double full = (double)(P.T - 1) * P.m * TW;
+            const double lc = target - cost0[a];
+            long long lu = lc <= full ? (long long)std::llround(lc / TW)
+                                      : (long long)(P.T - 1) * P.m + (long long)std::llround((lc - full) / (double)last_w);
+            lu = std::min(std::max<long long>(lu, 0), (long long)P.T * P.m);
+            u = L.unit0[a] + lu;
+        }
+        L.wbound[g] = std::max(L.wbound[g - 1], std::min(u, total));
+    }
+    L.wbound[G] = total;
+    L.fin_prob.assign(FB, -1);
+    L.fin_local.assign(FB, 0);
+    int fb = 0;
+    for (int x = 0; x < na; ++x) {
+        const drot::BatchProb &P = hp[active[x]];
+        for (int l = 0; l < P.fin_blocks && fb < FB; ++l, ++fb) {
+            L.fin_prob[fb] = active[x];
+            L.fin_local[fb] = l;
+        }
+    }
+}
+
+struct BatchDev {
+    drot::BatchProb *probs;
+    int *active, *nactive, *fin_prob, *fin_local, *flags;
+    long long *unit0, *wbound;
+};
+
+drot_status upload_lists(drot_handle *h, const BatchLists &L, const BatchDev &D, int FB) {
+    const int na = (int)L.active.size();
+    DROT_CUDA(h, cudaMemcpyAsync(D.nactive, &na, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (na > 0)
+        DROT_CUDA(h, cudaMemcpyAsync(D.active, L.active.data(), sizeof(int) * na, cudaMemcpyHostToDevice, h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(D.unit0, L.unit0.data(), sizeof(long long) * (na + 1), cudaMemcpyHostToDevice,
+                                 h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(D.wbound, L.wbound.data(), sizeof(long long) * L.wbound.size(),
+                                 cudaMemcpyHostToDevice, h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(D.fin_prob, L.fin_prob.data(), sizeof(int) * FB, cudaMemcpyHostToDevice, h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(D.fin_local, L.fin_local.data(), sizeof(int) * FB, cudaMemcpyHostToDevice,
+                                 h->stream));
+    // pageable sources: the copies return once the host data has been staged, but keep
+    // the stream ordered with the next launch anyway
+    return DROT_OK;
+}
+
+drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, double tol, long long max_iter,
+                                 int warm, drot_result *res) {
+    const int rule = (h->cfg.stop_rule & 7) ? (h->cfg.stop_rule & 7) : (DROT_STOP_GAP | DROT_STOP_RES_L1);
+    int thr[2] = {384, 1536};
+    if (h->batch_k_thresholds[0] > 0) {
+        thr[0] = h->batch_k_thresholds[0];
+        thr[1] = h->batch_k_thresholds[1];
+    }
+    // layout: scalars[B] | per problem: g a u (m), h b v (n), acc[2], finpart | tables
+    std::vector<drot::BatchProb> hp(B);
+    std::vector<size_t> off(B);
+    size_t bytes = align_up(sizeof(Scalars) * B, 256);
+    int FB = 0;
+    for (int b = 0; b < B; ++b) {
+        const long long m = pr[b].m, n = pr[b].n;
+        const int fb = (int)std::min<long long>(32, std::max<long long>(1, (m + n + 255) / 256));
+        hp[b].fin_blocks = fb;
+        FB += fb;
+        off[b] = bytes;
+        bytes += align_up(sizeof(double) * m, 256) * 3 + align_up(sizeof(double) * n, 256) * 3 + 256 +
+                 align_up(sizeof(double) * drot::kFinishAcc * fb, 256);
+    }
+    const size_t vec_bytes = bytes - align_up(sizeof(Scalars) * B, 256);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, drot::drot_batched_step_kernel<true>, drot::kThreads, 0);
+    const int G = std::max(1, occ) * h->num_sms;
+    const size_t tables = align_up(sizeof(drot::BatchProb) * B, 256) + align_up(sizeof(int) * B, 256) * 3 +
+                          align_up(sizeof(long long) * (B + 1), 256) + align_up(sizeof(long long) * (G + 1), 256) +
+                          align_up(sizeof(int) * FB, 256) * 2 + 256;
+    drot_status st = arena_reserve(h, h->batch, bytes + tables);
+    if (st != DROT_OK) return st;
+    if (h->h_bstat_cap < (size_t)B) {
+        if (h->h_bstat) cudaFreeHost(h->h_bstat);
+        h->h_bstat = nullptr;
+        h->h_bstat_cap = 0;
+        DROT_CUDA(h, cudaMallocHost(&h->h_bstat, sizeof(Scalars) * B));
+        h->h_bstat_cap = B;
+    }
+    char *base = static_cast<char *>(h->batch.ptr);
+    Scalars *d_sc = reinterpret_cast<Scalars *>(base);
+    for (int b = 0; b < B; ++b) {
+        char *cur = base + off[b];
+        const long long m = pr[b].m, n = pr[b].n;
+        drot::BatchProb &P = hp[b];
+        P.C = pr[b].C;
+        P.X = pr[b].X;
+        P.p = pr[b].p;
+        P.q = pr[b].q;
+        P.mu = pr[b].mu;
+        P.nu = pr[b].nu;
+        P.g = carve<double>(cur, m);
+        P.a = carve<double>(cur, m);
+        P.u = carve<double>(cur, m);
+        P.h = carve<double>(cur, n);
+        P.b = carve<double>(cur, n);
+        P.v = carve<double>(cur, n);
+        P.acc = carve<double>(cur, 2);
+        P.finpart = carve<double>(cur, (size_t)drot::kFinishAcc * P.fin_blocks);
+        P.sc = d_sc + b;
+        P.m = m;
+        P.n = n;
+        P.ld = pr[b].ld;
+        P.inv_n = 1.0 / (double)n;
+        P.inv_m = 1.0 / (double)m;
+        P.K = batch_k(n, thr);
+        P.T = (int)((n + 128LL * P.K - 1) / (128LL * P.K));
+    }
+    char *cur = base + bytes;
+    BatchDev D{};
+    D.probs = carve<drot::BatchProb>(cur, B);
+    D.active = carve<int>(cur, B);
+    D.flags = carve<int>(cur, B);
+    D.fin_prob = carve<int>(cur, FB);
+    D.fin_local = carve<int>(cur, FB);
+    D.unit0 = carve<long long>(cur, B + 1);
+    D.wbound = carve<long long>(cur, G + 1);
+    D.nactive = carve<int>(cur, 1);
+
+    // scalar state of every problem, then the marginal checks
+    std::vector<Scalars> hs(B);
+    for (int b = 0; b < B; ++b) {
+        std::memset(&hs[b], 0, sizeof(Scalars));
+        hs[b].rho = pr[b].rho > 0.0 ? pr[b].rho : h->cfg.rho0 / (double)(pr[b].m + pr[b].n);
+        hs[b].tol = tol;
+        hs[b].max_iter = max_iter;
+        hs[b].stop_rule = rule;
+        hs[b].done = drot::kRunning;
+    }
+    DROT_CUDA(h, cudaMemcpyAsync(d_sc, hs.data(), sizeof(Scalars) * B, cudaMemcpyHostToDevice, h->stream));
+    DROT_CUDA(h, cudaMemsetAsync(base + align_up(sizeof(Scalars) * B, 256), 0, vec_bytes, h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(D.probs, hp.data(), sizeof(drot::BatchProb) * B, cudaMemcpyHostToDevice, h->stream));
+    drot::drot_batched_vector_sums_kernel<<<B, 1024, 0, h->stream>>>(D.probs, warm);
+    DROT_CUDA(h, cudaGetLastError());
+    DROT_CUDA(h, cudaMemcpyAsync(h->h_bstat, d_sc, sizeof(Scalars) * B, cudaMemcpyDeviceToHost, h->stream));
+    DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->prof.kernel_launches += 1;
+    std::vector<drot_status> status(B, DROT_OK);
+    std::vector<int> valid;
+    for (int b = 0; b < B; ++b) {
+        const Scalars &c = h->h_bstat[b];
+        if (c.nonfinite_input & 3) status[b] = DROT_ERR_MARGINALS;
+        else if (c.nonfinite_input & 4) status[b] = DROT_ERR_INVALID_ARG;
+        else if (!(std::fabs(c.sum_p - c.sum_q) <= 1e-9 * std::max(1.0, std::fabs(c.sum_p))))
+            status[b] = DROT_ERR_MARGINALS;
+        else valid.push_back(b);
+    }
+    const int nvalid = (int)valid.size();
+
+    // cold start X_0 = p q^T, sums of X_0, a_0 / b_0 / alpha_0
+    std::vector<int> flags(B, 0);
+    for (int b : valid) flags[b] = warm ? 0 : 1;
+    DROT_CUDA(h, cudaMemcpyAsync(D.flags, flags.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+    if (!warm && nvalid > 0) {
+        drot::drot_batched_init_plan_kernel<<<dim3(64, B), 256, 0, h->stream>>>(D.probs, D.flags);
+        DROT_CUDA(h, cudaGetLastError());
+        h->prof.kernel_launches += 1;
+    }
+    BatchLists L;
+    build_batch_lists(hp, valid, G, FB, L);
+    st = upload_lists(h, L, D, FB);
+    if (st != DROT_OK) return st;
+    drot::BatchArgs A{};
+    A.probs = D.probs;
+    A.active = D.active;
+    A.unit0 = D.unit0;
+    A.wbound = D.wbound;
+    A.fin_prob = D.fin_prob;
+    A.fin_local = D.fin_local;
+    A.nactive = D.nactive;
+    A.warm = warm;
+    drot::drot_batched_step_kernel<false><<<G, drot::kThreads, 0, h->stream>>>(A);
+    DROT_CUDA(h, cudaGetLastError());
+    drot::drot_batched_init_state_kernel<<<FB, drot::kFinishThreads, 0, h->stream>>>(A);
+    DROT_CUDA(h, cudaGetLastError());
+    h->prof.kernel_launches += 2;
+
+    // graph of `gi` iterations over the active list
+    double bytes_iter = 0.0;
+    for (int b : valid) bytes_iter += 12.0 * (double)pr[b].m * (double)pr[b].n;
+    int gi = h->cfg.graph_iters;
+    if (gi <= 0) gi = (int)std::max(1L, std::min(256L, std::lround(4.0e-3 / (bytes_iter / 6.0e12 + 12.0e-6))));
+    if (h->bexec) {
+        cudaGraphExecDestroy(h->bexec);
+        h->bexec = nullptr;
+    }
+    if (max_iter > 0 && nvalid > 0) {
+        cudaGraph_t graph = nullptr;
+        DROT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t err = cudaSuccess;
+        for (int it = 0; it < gi && err == cudaSuccess; ++it) {
+            drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(A);
+            err = cudaGetLastError();
+            if (err == cudaSuccess) {
+                drot::drot_batched_finish_kernel<<<FB, drot::kFinishThreads, 0, h->stream>>>(A);
+                err = cudaGetLastError();
+            }
+        }
+        cudaError_t end = cudaStreamEndCapture(h->stream, &graph);
+        if (err != cudaSuccess || end != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, DROT_ERR_CUDA, "batched graph capture failed: %s",
+                        cudaGetErrorString(err != cudaSuccess ? err : end));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&h->bexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess)
+            return fail(h, DROT_ERR_CUDA, "batched graph instantiate failed: %s", cudaGetErrorString(ie));
+
+        std::vector<int> active = valid;
+        const long long max_replays = (max_iter + gi - 1) / gi + 2;
+        for (long long r = 0; r < max_replays && !active.empty(); ++r) {
+            DROT_CUDA(h, cudaGraphLaunch(h->bexec, h->stream));
+            h->prof.graph_replays += 1;
+            h->prof.kernel_launches += 2LL * gi;
+            DROT_CUDA(h, cudaMemcpyAsync(h->h_bstat, d_sc, sizeof(Scalars) * B, cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+            std::vector<int> still;
+            for (int b : active)
+                if (h->h_bstat[b].done == drot::kRunning) still.push_back(b);
+            if (still.size() != active.size() && !still.empty()) {
+                build_batch_lists(hp, still, G, FB, L);
+                st = upload_lists(h, L, D, FB);
+                if (st != DROT_OK) return st;
+            }
+            active.swap(still);
+        }
+        if (!active.empty())
+            return fail(h, DROT_ERR_CUDA, "%zu problems did not report completion", active.size());
+    }
+
+    // duals and nnz
+    if (nvalid > 0) {
+        for (int b : valid) flags[b] = 1;
+        DROT_CUDA(h, cudaMemcpyAsync(D.flags, flags.data(), sizeof(int) * B, cudaMemcpyHostToDevice, h->stream));
+        drot::drot_batched_export_kernel<<<dim3(32, B), 256, 0, h->stream>>>(D.probs, D.flags);
+        DROT_CUDA(h, cudaGetLastError());
+        h->prof.kernel_launches += 1;
+    }
+    DROT_CUDA(h, cudaMemcpyAsync(h->h_bstat, d_sc, sizeof(Scalars) * B, cudaMemcpyDeviceToHost, h->stream));
+    DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+    drot_status first_bad = DROT_OK;
+    for (int b = 0; b < B; ++b) {
+        const Scalars &c = h->h_bstat[b];
+        if (status[b] == DROT_OK) {
+            if (max_iter == 0 || c.done == drot::kIterCap) status[b] = DROT_NOT_CONVERGED;
+            else if (c.done == drot::kNonFinite) status[b] = DROT_ERR_NONFINITE;
+            else if (c.done == drot::kFault) status[b] = DROT_ERR_TIMEOUT;
+        }
+        if (status[b] != DROT_OK && first_bad == DROT_OK) first_bad = status[b];
+        if (res) {
+            drot_result &R = res[b];
+            R.iters = status[b] == DROT_OK || status[b] == DROT_NOT_CONVERGED || status[b] == DROT_ERR_NONFINITE
+                          ? c.k : 0;
+            R.primal_obj = c.primal;
+            R.dual_obj = c.dual;
+            R.gap = c.gap;
+            R.res_l1 = c.res_l1;
+            R.res_l2 = c.res_l2;
+            R.dual_res = c.dual_res_prev;
+            R.nnz = (int64_t)c.nnz;
+            R.status = status[b];
+            R.seconds = 0.0;
+            if (R.iters == 0) R.primal_obj = R.dual_obj = R.gap = R.res_l1 = R.res_l2 = R.dual_res = NAN;
+        }
+    }
+    return first_bad;
+}
+
 drot_status check_args(drot_handle *h, long long m, long long n, const float *C, long long ld, const double *p,
                        const double *q, double tol, long long max_iter, float *X, double *mu, double *nu) {
     if (!h) return DROT_ERR_INVALID_ARG;
@@ -568,6 +1025,8 @@ void drot_config_default(drot_config *cfg) {
     cfg->grid_ctas = 0;
     cfg->profile = 0;
     cfg->step_variant = 0;
+    cfg->deterministic = 0;
+    cfg->autotune = 0;
 }
 
 drot_status drot_create(drot_handle **out, const drot_config *cfg) {
@@ -593,6 +1052,7 @@ drot_status drot_create(drot_handle **out, const drot_config *cfg) {
     if (cudaSetDevice(h->device) != cudaSuccess) return bail(DROT_ERR_CUDA);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (set_kernel_attributes() != cudaSuccess) return bail(DROT_ERR_CUDA);
+    if (fill_occupancy(h) != cudaSuccess) return bail(DROT_ERR_CUDA);
     if (c.stream) {
         h->stream = static_cast<cudaStream_t>(c.stream);
     } else {
@@ -613,6 +1073,10 @@ drot_status drot_destroy(drot_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     destroy_graphs(h);
     if (h->work.ptr) cudaFree(h->work.ptr);
+    if (h->tune_x.ptr) cudaFree(h->tune_x.ptr);
+    if (h->batch.ptr) cudaFree(h->batch.ptr);
+    if (h->h_bstat) cudaFreeHost(h->h_bstat);
+    if (h->bexec) cudaGraphExecDestroy(h->bexec);
     if (h->staging.ptr) cudaFree(h->staging.ptr);
     if (h->d_sc) cudaFree(h->d_sc);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -675,19 +1139,40 @@ drot_status drot_solve(drot_handle *h, int64_t m, int64_t n, const float *C, int
 
 drot_status drot_solve_batched(drot_handle *h, int32_t B, const drot_problem *probs, double tol, int64_t max_iter,
                                int warm, drot_result *res) {
+    const auto t0 = std::chrono::steady_clock::now();
     if (!h || B < 0 || (B > 0 && !probs)) return DROT_ERR_INVALID_ARG;
-    drot_status first_bad = DROT_OK;
+    if (B == 0) return DROT_OK;
+    h->last_error.clear();
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, DROT_ERR_CUDA, "cudaSetDevice failed");
+    bool all_device = true;
     for (int32_t b = 0; b < B; ++b) {
         const drot_problem &P = probs[b];
-        drot_result r{};
-        drot_status st = drot_solve(h, P.m, P.n, P.C, P.ld, P.p, P.q, P.rho, tol, max_iter, P.X, P.mu, P.nu, warm,
-                                    res ? &r : nullptr);
-        if (res) {
-            r.status = st;
-            res[b] = r;
+        drot_status st = check_args(h, P.m, P.n, P.C, P.ld, P.p, P.q, tol, max_iter, P.X, P.mu, P.nu);
+        if (st != DROT_OK) return fail(h, st, "problem %d: %s", (int)b, h->last_error.c_str());
+        const void *ptrs[6] = {P.C, P.p, P.q, P.X, P.mu, P.nu};
+        for (const void *ptr : ptrs) all_device = all_device && is_device_ptr(ptr, h->device);
+    }
+    drot_status first_bad = DROT_OK;
+    if (all_device) {
+        first_bad = solve_batched_device(h, B, probs, tol, max_iter, warm, res);
+    } else {
+        // host buffers: one problem at a time through the staging path of drot_solve
+        for (int32_t b = 0; b < B; ++b) {
+            const drot_problem &P = probs[b];
+            drot_result r{};
+            drot_status st = drot_solve(h, P.m, P.n, P.C, P.ld, P.p, P.q, P.rho, tol, max_iter, P.X, P.mu, P.nu,
+                                        warm, res ? &r : nullptr);
+            if (res) {
+                r.status = st;
+                res[b] = r;
+            }
+            if (st != DROT_OK && first_bad == DROT_OK) first_bad = st;
+            if (st != DROT_OK && st != DROT_NOT_CONVERGED && st != DROT_ERR_NONFINITE) return st;
         }
-        if (st != DROT_OK && first_bad == DROT_OK) first_bad = st;
-        if (st != DROT_OK && st != DROT_NOT_CONVERGED && st != DROT_ERR_NONFINITE) return st;
+    }
+    if (res && all_device) {
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int32_t b = 0; b < B; ++b) res[b].seconds = secs;
     }
     return first_bad;
 }

@@ -1,0 +1,312 @@
+// Device code of the batched DROT solver: many independent problems of uneven
+// sizes advanced together, one fused-step launch and one finish launch per
+// iteration for all problems that have not stopped yet.
+//
+// Each problem runs Algorithm 1 (Sec. 3.1) exactly as the single-problem solver
+// does (same per-entry arithmetic, same FP64 totals in accumulation mode, its own
+// scalar state, stopping test and flag).  What is shared is the launch: the row
+// segments of all active problems form one list (problem-major, then tile-major,
+// then row), the host cuts that list into one contiguous, byte-balanced range per
+// CTA, and each CTA walks its range segment by segment, taking the tile width of
+// the problem a segment belongs to.  The finish launch gives each active problem
+// its own group of blocks; the last block of a group closes that problem's
+// iteration.  Converged problems are dropped from the lists between graph replays
+// (and their segments skipped inside a replay), so the work of a launch shrinks as
+// problems finish.
+#pragma once
+
+#include "drot_kernels.cuh"
+
+namespace drot {
+
+// Per-problem device descriptor (fixed for the whole batched call).
+struct BatchProb {
+    const float* C;
+    float* X;
+    const double* p;
+    const double* q;
+    double* mu;             // warm-start duals on entry, duals on exit
+    double* nu;
+    double *g, *h, *a, *b;  // phi/psi numerators and the a, b state vectors
+    double *u, *v;          // row / column totals (FP64 atomics), reset by the finish pass
+    double* acc;            // [2] <C,X> and sum [d]_+^2 (FP64 atomics)
+    double* finpart;        // [fin_blocks][kFinishAcc]
+    Scalars* sc;
+    long long m, n, ld;
+    double inv_n, inv_m;
+    int K;                  // float4 chunks per lane (tile width 128 K)
+    int T;                  // column tiles
+    int fin_blocks;         // blocks of the finish launch serving this problem
+    int pad;
+};
+
+// Work lists of the current replay (rebuilt by the host between replays).
+struct BatchArgs {
+    const BatchProb* probs;
+    const int* active;         // [nactive] problem indices, in segment-list order
+    const long long* unit0;    // [nactive + 1] first segment of each active problem; unit0[nactive] = total
+    const long long* wbound;   // [G + 1] segment range of each step CTA
+    const int* fin_prob;       // [FB] problem served by each finish block (-1: idle)
+    const int* fin_local;      // [FB] index of the block within its problem's group
+    const int* nactive;        // number of active problems (device, updated between replays)
+    int warm;
+};
+
+__device__ __forceinline__ FinishArgs batch_finish_args(const BatchProb& P) {
+    FinishArgs F{};
+    F.u = P.u;
+    F.v = P.v;
+    F.acc = P.acc;
+    F.accumulate = 1;
+    F.p = P.p;
+    F.q = P.q;
+    F.a = P.a;
+    F.b = P.b;
+    F.g = P.g;
+    F.h = P.h;
+    F.finpart = P.finpart;
+    F.sc = P.sc;
+    F.m = P.m;
+    F.n = P.n;
+    F.inv_n = P.inv_n;
+    F.inv_m = P.inv_m;
+    return F;
+}
+
+// Fused DR pass over every active problem (UPDATE = false: row/column sums of
+// X_0 only, used once at initialisation).
+template <bool UPDATE>
+__global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArgs B) {
+    constexpr int KMAX = 4;
+    __shared__ double s_col[kWarps][128 * KMAX];
+    __shared__ double s_red[kWarps][2];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long w0 = B.wbound[blockIdx.x];
+    const long long w1 = B.wbound[blockIdx.x + 1];
+    const int nactive = *B.nactive;
+    if (w0 >= w1 || nactive <= 0) return;
+
+    // the active problem holding w0: the last a with unit0[a] <= w0
+    int lo = 0, hi = nactive - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.unit0[mid] <= w0) lo = mid;
+        else hi = mid - 1;
+    }
+    int ai = lo;
+    long long w = w0;
+    while (w < w1) {
+        while (ai + 1 < nactive && w >= B.unit0[ai + 1]) ++ai;
+        const BatchProb& P = B.probs[B.active[ai]];
+        const long long base = B.unit0[ai];
+        const long long m = P.m, n = P.n, ld = P.ld;
+        const long long t = (w - base) / m;
+        const long long seg_end = min(w1, base + (t + 1) * m);
+        const long long i0 = w - base - t * m, i1 = seg_end - base - t * m;
+        w = seg_end;
+        if (P.sc->done != kRunning) continue;  // uniform: every thread reads the same flag
+
+        const int K = P.K;
+        const int TW = 128 * K;
+        const long long col0 = t * TW;
+        const double cs = P.sc->c;
+        const float rho = UPDATE ? (float)P.sc->rho : 0.f;
+
+        float psi[KMAX][4], cacc[KMAX][4];
+#pragma unroll
+        for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const long long j = col0 + kk * 128 + lane * 4 + e;
+                psi[kk][e] = (UPDATE && kk < K && j < n) ? (float)((P.h[j] + cs) * P.inv_m) : 0.f;
+                cacc[kk][e] = 0.f;
+            }
+        for (int x = lane; x < TW; x += 32) s_col[warp][x] = 0.0;
+        __syncwarp();
+
+        float scx = 0.f, sd = 0.f;
+        double scx64 = 0.0, sd64 = 0.0;
+        int since_flush = 0;
+        for (long long i = i0 + warp; i < i1; i += kWarps) {
+            const float phi = UPDATE ? (float)((P.g[i] + cs) * P.inv_n) : 0.f;
+            const long long rowoff = i * ld + col0 + lane * 4;
+            float4 xv[KMAX], cv[KMAX];
+#pragma unroll
+            for (int kk = 0; kk < KMAX; ++kk) {
+                if (kk < K && col0 + kk * 128 + lane * 4 < n) {
+                    xv[kk] = *reinterpret_cast<const float4*>(P.X + rowoff + kk * 128);
+                    if (UPDATE) cv[kk] = ld_stream_ro(P.C + rowoff + kk * 128);
+                }
+            }
+            float rs = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < KMAX; ++kk) {
+                const long long j = col0 + kk * 128 + lane * 4;
+                if (kk < K && j < n) {
+                    float xs[4] = {xv[kk].x, xv[kk].y, xv[kk].z, xv[kk].w};
+                    float cc[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (UPDATE) { cc[0] = cv[kk].x; cc[1] = cv[kk].y; cc[2] = cv[kk].z; cc[3] = cv[kk].w; }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (j + e < n) {
+                            float xn = xs[e];
+                            if (UPDATE) {
+                                const float d = fmaf(-rho, cc[e], phi + psi[kk][e]);
+                                xn = fmaxf(xs[e] + d, 0.f);
+                                scx = fmaf(cc[e], xn, scx);
+                                const float dp = fmaxf(d, 0.f);
+                                sd = fmaf(dp, dp, sd);
+                                xs[e] = xn;
+                            }
+                            rs += xn;
+                            cacc[kk][e] += xn;
+                        }
+                    }
+                    if (UPDATE) {
+                        float* dst = P.X + rowoff + kk * 128;
+                        if (j + 3 < n) {
+                            *reinterpret_cast<float4*>(dst) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (j + e < n) dst[e] = xs[e];
+                        }
+                    }
+                }
+            }
+            rs = warp_sum_f32(rs);
+            if (lane == 0) atomicAdd(P.u + i, (double)rs);
+            if (++since_flush == kFlushRows) {
+#pragma unroll
+                for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (kk < K) {
+                            s_col[warp][kk * 128 + lane * 4 + e] += (double)cacc[kk][e];
+                            cacc[kk][e] = 0.f;
+                        }
+                scx64 += (double)scx;
+                sd64 += (double)sd;
+                scx = 0.f;
+                sd = 0.f;
+                since_flush = 0;
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (kk < K) s_col[warp][kk * 128 + lane * 4 + e] += (double)cacc[kk][e];
+        scx64 += (double)scx;
+        sd64 += (double)sd;
+        __syncthreads();
+        for (int x = threadIdx.x; x < TW; x += kThreads) {
+            double v = 0.0;
+#pragma unroll
+            for (int wv = 0; wv < kWarps; ++wv) v += s_col[wv][x];
+            if (col0 + x < n) atomicAdd(P.v + col0 + x, v);
+        }
+        if (UPDATE) {
+            double v2[2] = {scx64, sd64};
+            block_sum_f64<2, kThreads>(v2, s_red);  // ends with a block barrier
+            if (threadIdx.x == 0) {
+                atomicAdd(P.acc + 0, v2[0]);
+                atomicAdd(P.acc + 1, v2[1]);
+            }
+        } else {
+            __syncthreads();
+        }
+    }
+}
+
+// Steps 5-8 and the stopping test of every active problem (one block group each).
+__global__ void __launch_bounds__(kFinishThreads) drot_batched_finish_kernel(BatchArgs B) {
+    const int pi = B.fin_prob[blockIdx.x];
+    if (pi < 0) return;
+    const BatchProb& P = B.probs[pi];
+    if (P.sc->done != kRunning) return;
+    finish_body(batch_finish_args(P), B.fin_local[blockIdx.x], P.fin_blocks);
+}
+
+// a_0, b_0, alpha_0 and the numerators of phi_0, psi_0 of every active problem.
+__global__ void __launch_bounds__(kFinishThreads) drot_batched_init_state_kernel(BatchArgs B) {
+    const int pi = B.fin_prob[blockIdx.x];
+    if (pi < 0) return;
+    const BatchProb& P = B.probs[pi];
+    init_state_body(batch_finish_args(P), B.warm ? P.mu : nullptr, B.warm ? P.nu : nullptr,
+                    B.fin_local[blockIdx.x], P.fin_blocks);
+}
+
+// Marginal (and warm-dual) sums: one block per problem of the batch.
+__global__ void __launch_bounds__(1024) drot_batched_vector_sums_kernel(const BatchProb* probs, int warm) {
+    const BatchProb& P = probs[blockIdx.x];
+    __shared__ double s_red[32][6];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long i = threadIdx.x; i < P.m; i += blockDim.x) {
+        v[0] += P.p[i];
+        if (!(P.p[i] >= 0.0) || !isfinite(P.p[i])) v[4] += 1.0;
+        if (warm) v[2] += P.mu[i];
+    }
+    for (long long j = threadIdx.x; j < P.n; j += blockDim.x) {
+        v[1] += P.q[j];
+        if (!(P.q[j] >= 0.0) || !isfinite(P.q[j])) v[5] += 1.0;
+        if (warm) v[3] += P.nu[j];
+    }
+    block_sum_f64<6, 1024>(v, s_red);
+    if (threadIdx.x == 0) {
+        Scalars* sc = P.sc;
+        sc->sum_p = v[0];
+        sc->sum_q = v[1];
+        sc->sum_phi0 = sc->rho * v[2];
+        sc->sum_psi0 = sc->rho * v[3];
+        sc->nonfinite_input = (v[4] > 0.0 ? 1 : 0) | (v[5] > 0.0 ? 2 : 0) |
+                              ((isfinite(v[2]) && isfinite(v[3])) ? 0 : 4);
+    }
+}
+
+// X_0 = p q^T for every problem flagged in `cold` (blockIdx.y = problem).
+__global__ void drot_batched_init_plan_kernel(const BatchProb* probs, const int* cold) {
+    const BatchProb& P = probs[blockIdx.y];
+    if (!cold[blockIdx.y]) return;
+    const long long m = P.m, n = P.n, ld = P.ld;
+    const long long nv = (n + 3) / 4;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < m * nv;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / nv;
+        const long long j = (idx - i * nv) * 4;
+        const double pi = P.p[i];
+        float* dst = P.X + i * ld + j;
+        if (j + 3 < n) {
+            *reinterpret_cast<float4*>(dst) = make_float4((float)(pi * P.q[j]), (float)(pi * P.q[j + 1]),
+                                                          (float)(pi * P.q[j + 2]), (float)(pi * P.q[j + 3]));
+        } else {
+            for (int e = 0; e < 4; ++e)
+                if (j + e < n) dst[e] = (float)(pi * P.q[j + e]);
+        }
+    }
+}
+
+// mu = phi / rho, nu = psi / rho and nnz(X) of every problem (blockIdx.y = problem).
+__global__ void drot_batched_export_kernel(const BatchProb* probs, const int* live) {
+    const BatchProb& P = probs[blockIdx.y];
+    if (!live[blockIdx.y]) return;
+    const Scalars* sc = P.sc;
+    const double c = sc->c, rho = sc->rho;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < P.m + P.n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (idx < P.m) P.mu[idx] = (P.g[idx] + c) * P.inv_n / rho;
+        else P.nu[idx - P.m] = (P.h[idx - P.m] + c) * P.inv_m / rho;
+    }
+    unsigned long long cnt = 0;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < P.m * P.n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / P.n, j = idx - i * P.n;
+        cnt += P.X[i * P.ld + j] > 0.f ? 1ull : 0ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&P.sc->nnz, cnt);
+}
+
+}  // namespace drot

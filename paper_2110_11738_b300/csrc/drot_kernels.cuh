@@ -75,6 +75,10 @@ struct StepArgs {
     double* rowpart;            // [T][m]
     double* colpart;            // [slots][TW]
     double* ctapart;            // [G][2]: <C,X> and sum [d]_+^2 per CTA
+    double* u;                  // accumulation mode: row totals (m), added with FP64 atomics
+    double* v;                  // accumulation mode: column totals (n)
+    double* acc;                // accumulation mode: [2] <C,X> and sum [d]_+^2
+    int accumulate;             // 1: atomics into u, v, acc; 0: fixed-order partials
     const long long* wbound;    // [G+1] segment range of each CTA
     const int* slot_base;       // [G]   first slot of each CTA
     long long m, n, ld;
@@ -92,6 +96,13 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// Partial-sum sinks of the fused step.  Fixed-order mode writes one partial per
+// (column tile, row), per (CTA, tile) and per CTA, each with a single writer, for
+// the finish kernel to add in a fixed order (bitwise reproducible).  Accumulation
+// mode adds them into the totals with FP64 atomic adds as they are produced, so
+// the finish kernel reads one value per row and column.
+struct StepArgs;
 
 // Block-wide sum of NV doubles in a fixed order; result valid in thread 0.
 template <int NV, int NT>
@@ -209,7 +220,10 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
                 }
             }
             rs = warp_sum_f32(rs);
-            if (lane == 0) A.rowpart[t * m + i] = (double)rs;
+            if (lane == 0) {
+                if (A.accumulate) atomicAdd(A.u + i, (double)rs);
+                else A.rowpart[t * m + i] = (double)rs;
+            }
             if (++since_flush == kFlushRows) {
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk)
@@ -237,7 +251,8 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
             double v = 0.0;
 #pragma unroll
             for (int wv = 0; wv < kWarps; ++wv) v += s_col[wv][x];
-            out[x] = v;
+            if (!A.accumulate) out[x] = v;
+            else if (col0 + x < n) atomicAdd(A.v + col0 + x, v);
         }
         __syncthreads();
         ++slot;
@@ -248,8 +263,13 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
         double v[2] = {scx64, sd64};
         block_sum_f64<2, kThreads>(v, s_red);
         if (threadIdx.x == 0) {
-            A.ctapart[2 * blockIdx.x + 0] = v[0];
-            A.ctapart[2 * blockIdx.x + 1] = v[1];
+            if (A.accumulate) {
+                atomicAdd(A.acc + 0, v[0]);
+                atomicAdd(A.acc + 1, v[1]);
+            } else {
+                A.ctapart[2 * blockIdx.x + 0] = v[0];
+                A.ctapart[2 * blockIdx.x + 1] = v[1];
+            }
         }
     }
 }
@@ -478,7 +498,10 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
                         }
                     }
                     rs = warp_sum_f32(rs);
-                    if (lane == 0) A.rowpart[t * m + i] = (double)rs;
+                    if (lane == 0) {
+                        if (A.accumulate) atomicAdd(A.u + i, (double)rs);
+                        else A.rowpart[t * m + i] = (double)rs;
+                    }
                     if (++since_flush == kFlushRows) {
 #pragma unroll
                         for (int kk = 0; kk < K; ++kk)
@@ -509,7 +532,8 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
                 double v = 0.0;
 #pragma unroll
                 for (int wv = 0; wv < kWarps; ++wv) v += s_col[wv * TW + x];
-                out[x] = v;
+                if (!A.accumulate) out[x] = v;
+                else if (col0 + x < n) atomicAdd(A.v + col0 + x, v);
             }
             consumer_sync();
             ++slot;
@@ -520,8 +544,13 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
     double v[2] = {scx64, sd64};
     block_sum_f64<2, kThreads + 32>(v, s_red);
     if (threadIdx.x == 0) {
-        A.ctapart[2 * blockIdx.x + 0] = v[0];
-        A.ctapart[2 * blockIdx.x + 1] = v[1];
+        if (A.accumulate) {
+            atomicAdd(A.acc + 0, v[0]);
+            atomicAdd(A.acc + 1, v[1]);
+        } else {
+            A.ctapart[2 * blockIdx.x + 0] = v[0];
+            A.ctapart[2 * blockIdx.x + 1] = v[1];
+        }
         if (s_abort) {
             // after a give-up, let the copies already issued land before the
             // block's shared memory is released (each wait bounded as well)
@@ -537,6 +566,10 @@ struct FinishArgs {
     const double* rowpart;
     const double* colpart;
     const double* ctapart;
+    double* u;              // accumulation mode: row totals, read and reset to 0
+    double* v;              // accumulation mode: column totals, read and reset to 0
+    double* acc;            // accumulation mode: [2] <C,X>, sum [d]_+^2, read and reset
+    int accumulate;
     const int* tile_slot;   // [T+1] first slot of each column tile
     const double* p;
     const double* q;
@@ -577,10 +610,20 @@ __device__ __forceinline__ double strided_total(const double* base, long long st
 }
 
 __device__ __forceinline__ double row_total(const FinishArgs& A, long long i) {
+    if (A.accumulate) {
+        const double u = A.u[i];
+        A.u[i] = 0.0;
+        return u;
+    }
     return strided_total(A.rowpart + i, A.m, A.T);
 }
 
 __device__ __forceinline__ double col_total(const FinishArgs& A, long long j) {
+    if (A.accumulate) {
+        const double v = A.v[j];
+        A.v[j] = 0.0;
+        return v;
+    }
     const long long t = j / A.TW;
     const long long jj = j - t * A.TW;
     const int s0 = A.tile_slot[t];
@@ -589,30 +632,30 @@ __device__ __forceinline__ double col_total(const FinishArgs& A, long long j) {
 
 // Returns true in every thread of the block that arrived last (all blocks'
 // finpart rows are then visible).  No block waits for another.
-__device__ __forceinline__ bool arrive_last(Scalars* sc) {
+__device__ __forceinline__ bool arrive_last(Scalars* sc, int nblk) {
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int ticket = atomicAdd(&sc->counter, 1u);
-        s_last = (ticket == gridDim.x - 1) ? 1 : 0;
+        s_last = (ticket == (unsigned int)nblk - 1u) ? 1 : 0;
     }
     __syncthreads();
     if (s_last) __threadfence();
     return s_last != 0;
 }
 
-// Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1).
-__global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs A) {
+// Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1), executed by block
+// `blk` of the `nblk` blocks that serve this problem.
+__device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nblk) {
     __shared__ double s_red[kFinishThreads / 32][kFinishAcc];
     Scalars* sc = A.sc;
-    if (sc->done != kRunning) return;
 
     // acc: 0 sum r, 1 ||r||_1 + ||s||_1, 2 ||r||^2 + ||s||^2, 3 p.g', 4 q.h', 5 sum s
     double acc[kFinishAcc] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const long long mn = A.m + A.n;
-    for (long long idx = (long long)blockIdx.x * kFinishThreads + threadIdx.x; idx < mn;
-         idx += (long long)gridDim.x * kFinishThreads) {
+    for (long long idx = (long long)blk * kFinishThreads + threadIdx.x; idx < mn;
+         idx += (long long)nblk * kFinishThreads) {
         if (idx < A.m) {
             const long long i = idx;
             const double r = row_total(A, i) - A.p[i];
@@ -638,19 +681,28 @@ __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs 
     block_sum_f64<kFinishAcc, kFinishThreads>(acc, s_red);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int c = 0; c < kFinishAcc; ++c) A.finpart[blockIdx.x * kFinishAcc + c] = acc[c];
+        for (int c = 0; c < kFinishAcc; ++c) A.finpart[blk * kFinishAcc + c] = acc[c];
     }
-    if (!arrive_last(sc)) return;
+    if (!arrive_last(sc, nblk)) return;
 
     // Last block: fixed-order totals over the blocks of this launch and the
     // CTAs of the step launch.
     double tot[kFinishAcc + 2];
     for (int c = 0; c < kFinishAcc + 2; ++c) tot[c] = 0.0;
-    for (int bidx = threadIdx.x; bidx < (int)gridDim.x; bidx += kFinishThreads)
+    for (int bidx = threadIdx.x; bidx < nblk; bidx += kFinishThreads)
         for (int c = 0; c < kFinishAcc; ++c) tot[c] += __ldcg(A.finpart + bidx * kFinishAcc + c);
-    for (int bidx = threadIdx.x; bidx < A.G; bidx += kFinishThreads) {
-        tot[kFinishAcc + 0] += __ldcg(A.ctapart + 2 * bidx + 0);
-        tot[kFinishAcc + 1] += __ldcg(A.ctapart + 2 * bidx + 1);
+    if (A.accumulate) {
+        if (threadIdx.x == 0) {
+            tot[kFinishAcc + 0] = __ldcg(A.acc + 0);
+            tot[kFinishAcc + 1] = __ldcg(A.acc + 1);
+            A.acc[0] = 0.0;
+            A.acc[1] = 0.0;
+        }
+    } else {
+        for (int bidx = threadIdx.x; bidx < A.G; bidx += kFinishThreads) {
+            tot[kFinishAcc + 0] += __ldcg(A.ctapart + 2 * bidx + 0);
+            tot[kFinishAcc + 1] += __ldcg(A.ctapart + 2 * bidx + 1);
+        }
     }
     __shared__ double s_red2[kFinishThreads / 32][kFinishAcc + 2];
     block_sum_f64<kFinishAcc + 2, kFinishThreads>(tot, s_red2);
@@ -692,6 +744,11 @@ __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs 
         __threadfence();
         sc->done = done;
     }
+}
+
+__global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs A) {
+    if (A.sc->done != kRunning) return;
+    finish_body(A, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- set-up / tear-down
@@ -748,16 +805,16 @@ __global__ void __launch_bounds__(1024) drot_vector_sums_kernel(const double* p,
 // psi_0 = rho nu_0), the numerators g = n phi_0, h = m psi_0, c_0 = 0 and
 // alpha_0 = f^T a_0 / (m + n).  Row and column sums of X_0 come from a
 // preceding UPDATE = false pass of the step kernel.
-__global__ void __launch_bounds__(kFinishThreads) drot_init_state_kernel(FinishArgs A, const double* mu0,
-                                                                         const double* nu0) {
+__device__ __forceinline__ void init_state_body(const FinishArgs& A, const double* mu0, const double* nu0, int blk,
+                                                int nblk) {
     __shared__ double s_red[kFinishThreads / 32][1];
     Scalars* sc = A.sc;
     const double rho = sc->rho;
     const double nd = (double)A.n, md = (double)A.m;
     double acc[1] = {0.0};
     const long long mn = A.m + A.n;
-    for (long long idx = (long long)blockIdx.x * kFinishThreads + threadIdx.x; idx < mn;
-         idx += (long long)gridDim.x * kFinishThreads) {
+    for (long long idx = (long long)blk * kFinishThreads + threadIdx.x; idx < mn;
+         idx += (long long)nblk * kFinishThreads) {
         if (idx < A.m) {
             const long long i = idx;
             const double phi0 = mu0 ? rho * mu0[i] : 0.0;
@@ -773,10 +830,10 @@ __global__ void __launch_bounds__(kFinishThreads) drot_init_state_kernel(FinishA
         }
     }
     block_sum_f64<1, kFinishThreads>(acc, s_red);
-    if (threadIdx.x == 0) A.finpart[blockIdx.x * kFinishAcc] = acc[0];
-    if (!arrive_last(sc)) return;
+    if (threadIdx.x == 0) A.finpart[blk * kFinishAcc] = acc[0];
+    if (!arrive_last(sc, nblk)) return;
     double tot[1] = {0.0};
-    for (int bidx = threadIdx.x; bidx < (int)gridDim.x; bidx += kFinishThreads)
+    for (int bidx = threadIdx.x; bidx < nblk; bidx += kFinishThreads)
         tot[0] += __ldcg(A.finpart + bidx * kFinishAcc);
     __shared__ double s_red2[kFinishThreads / 32][1];
     block_sum_f64<1, kFinishThreads>(tot, s_red2);
@@ -787,6 +844,11 @@ __global__ void __launch_bounds__(kFinishThreads) drot_init_state_kernel(FinishA
         sc->counter = 0u;
         sc->done = kRunning;
     }
+}
+
+__global__ void __launch_bounds__(kFinishThreads) drot_init_state_kernel(FinishArgs A, const double* mu0,
+                                                                         const double* nu0) {
+    init_state_body(A, mu0, nu0, blockIdx.x, gridDim.x);
 }
 
 // mu = phi / rho, nu = psi / rho (Appendix A.2, eq. dual:var).

@@ -46,7 +46,8 @@ EXPORTED = ("drot_config_default", "drot_create", "drot_solve", "drot_solve_batc
 class DrotConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("stop_rule", ctypes.c_int),
                 ("rho0", ctypes.c_double), ("graph_iters", ctypes.c_int), ("tile_k", ctypes.c_int),
-                ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int), ("step_variant", ctypes.c_int)]
+                ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int), ("step_variant", ctypes.c_int),
+                ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class DrotResult(ctypes.Structure):
@@ -66,7 +67,8 @@ class DrotProfile(ctypes.Structure):
     _fields_ = [("step_ms_total", ctypes.c_double), ("step_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("tile_k", ctypes.c_int32), ("grid_ctas", ctypes.c_int32), ("col_tiles", ctypes.c_int32),
-                ("graph_iters", ctypes.c_int32), ("step_variant", ctypes.c_int32), ("stages", ctypes.c_int32)]
+                ("graph_iters", ctypes.c_int32), ("step_variant", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("finish_ms_total", ctypes.c_double), ("iter_ms_total", ctypes.c_double)]
 
 
 class DrotError(RuntimeError):
@@ -137,7 +139,8 @@ STOP_DUAL_RES = 4
 
 def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = STOP_GAP | STOP_RES_L1,
                 rho0: float = 2.0, graph_iters: int = 0, tile_k: int = 0, grid_ctas: int = 0,
-                profile: bool = False, step_variant: int = 0) -> int:
+                profile: bool = False, step_variant: int = 0, deterministic: bool = False,
+                autotune: bool = False) -> int:
     """Create a solver handle; returns the opaque handle as an int."""
     lib = load()
     cfg = DrotConfig()
@@ -151,6 +154,8 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
     cfg.grid_ctas = int(grid_ctas)
     cfg.profile = int(bool(profile))
     cfg.step_variant = int(step_variant)
+    cfg.deterministic = int(bool(deterministic))
+    cfg.autotune = int(bool(autotune))
     h = ctypes.c_void_p()
     st = lib.drot_create(ctypes.byref(h), ctypes.byref(cfg))
     if st != DROT_OK:

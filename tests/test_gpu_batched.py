@@ -1,0 +1,110 @@
+"""Batched solver (drot_solve_batched on device buffers) against the single-problem solver
+and the FP64 oracle.
+
+Each problem of a batch runs Algorithm 1 (Sec. 3.1) with its own state and stopping test;
+only the launches are shared.  So every problem must match (a) the oracle step by step from
+a seeded start and (b) drot_solve on the same problem at convergence."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from paper_2110_11738_b300 import drot
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+def _dev_problem(pr, X0=None, mu0=None, nu0=None):
+    ld = workloads.pad_ld(pr.n)
+    Cb = torch.zeros((pr.m, ld), dtype=torch.float32, device="cuda")
+    Cb[:, : pr.n] = torch.as_tensor(pr.C)
+    Xb = torch.zeros_like(Cb)
+    if X0 is not None:
+        Xb[:, : pr.n] = torch.as_tensor(X0)
+    mu = torch.as_tensor(np.zeros(pr.m) if mu0 is None else mu0, dtype=torch.float64, device="cuda").clone()
+    nu = torch.as_tensor(np.zeros(pr.n) if nu0 is None else nu0, dtype=torch.float64, device="cuda").clone()
+    return dict(C=Cb[:, : pr.n], X=Xb[:, : pr.n], p=torch.as_tensor(pr.p, device="cuda"),
+                q=torch.as_tensor(pr.q, device="cuda"), mu=mu, nu=nu, rho=pr.rho)
+
+
+def _shapes():
+    return [(1, 1), (3, 7), (64, 2048), (517, 63), (200, 1029), (1000, 130), (33, 4100), (257, 257)]
+
+
+def test_batched_step_parity_with_oracle():
+    probs, starts, specs = [], [], []
+    for b, (m, n) in enumerate(_shapes()):
+        pr = workloads.make_problem("plain_8192x6144", seed=100 + b, m=m, n=n)
+        X0, mu0, nu0 = workloads.random_start(m, n, seed=200 + b)
+        probs.append(_dev_problem(pr, X0, mu0, nu0))
+        starts.append((X0, mu0, nu0))
+        specs.append(pr)
+    with drot.Solver(device=0) as s:
+        res = s.solve_batched(probs, tol=-1.0, max_iter=3, warm=True)
+    for pr, P, (X0, mu0, nu0), r in zip(specs, probs, starts, res):
+        assert r["status"] == drot.DROT_NOT_CONVERGED and r["iters"] == 3
+        ref = oracle.drot_run(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, 3, X0=X0.astype(np.float64),
+                              mu0=mu0, nu0=nu0)
+        S = max(np.abs(X0).max(), pr.rho * (np.abs(mu0).max() + np.abs(nu0).max() + 1.0), np.abs(ref["X"]).max())
+        Xg = P["X"].cpu().numpy().astype(np.float64)
+        assert np.abs(Xg - ref["X"]).max() <= 8 * EPS32 * S * 3 * 4
+        assert np.abs(P["mu"].cpu().numpy() - ref["mu"]).max() <= 64 * EPS32 * S / pr.rho * 3 + 1e-12
+        assert np.abs(P["nu"].cpu().numpy() - ref["nu"]).max() <= 64 * EPS32 * S / pr.rho * 3 + 1e-12
+        h = ref["history"][-1]
+        assert abs(r["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9
+
+
+def test_batched_solves_match_single_solves():
+    specs = [workloads.make_problem("plain_256", seed=s, m=m, n=n)
+             for s, (m, n) in enumerate([(40, 60), (96, 80), (61, 190), (128, 128), (20, 300)])]
+    probs = [_dev_problem(pr) for pr in specs]
+    with drot.Solver(device=0) as s:
+        res = s.solve_batched(probs, tol=1e-6, max_iter=2_000_000)
+        for pr, P, r in zip(specs, probs, res):
+            assert r["status"] == drot.DROT_OK, r
+            Q = _dev_problem(pr)
+            one = s.solve(Q["C"], Q["p"], Q["q"], rho=pr.rho, tol=1e-6, max_iter=2_000_000, X=Q["X"], mu=Q["mu"],
+                          nu=Q["nu"])
+            assert one["status"] == drot.DROT_OK
+            obj = one["primal_obj"]
+            assert abs(r["primal_obj"] - obj) <= 1e-5 * abs(obj)
+            assert abs(r["iters"] - one["iters"]) <= 0.05 * one["iters"] + 5
+            Xg = P["X"].cpu().numpy().astype(np.float64)
+            st = oracle.plan_stats(pr.C.astype(np.float64), pr.p, pr.q, Xg, P["mu"].cpu().numpy(),
+                                   P["nu"].cpu().numpy())
+            assert st["res_l1"] <= 1.5e-6 and st["gap"] <= 1.5e-6
+            assert r["nnz"] == int((Xg > 0).sum())
+
+
+def test_batched_reports_per_problem_status():
+    good = workloads.make_problem("plain_256", seed=1, m=30, n=40)
+    bad = workloads.make_problem("plain_256", seed=2, m=30, n=40)
+    P_good, P_bad = _dev_problem(good), _dev_problem(bad)
+    P_bad["q"] = P_bad["q"] * 1.5  # mass mismatch
+    with drot.Solver(device=0) as s:
+        res = s.solve_batched([P_good, P_bad, _dev_problem(good)], tol=1e-6, max_iter=1_000_000, check=False)
+    assert res[0]["status"] == drot.DROT_OK and res[2]["status"] == drot.DROT_OK
+    assert res[1]["status"] == drot.DROT_ERR_MARGINALS
+    assert res[0]["primal_obj"] == pytest.approx(res[2]["primal_obj"], rel=1e-6)
+
+
+def test_batched_uneven_config_subset_iteration_cap():
+    # 24 problems drawn like the 512-problem workload (m, n uniform in [64, 2048], shifted
+    # clouds, Dirichlet marginals), a fixed iteration budget: every problem must agree with
+    # its own single solve after the same number of iterations
+    specs = workloads.make_batch(B=24, seed=3)
+    probs = [_dev_problem(pr) for pr in specs]
+    with drot.Solver(device=0) as s:
+        res = s.solve_batched(probs, tol=-1.0, max_iter=200)
+        for pr, P, r in zip(specs[:6], probs[:6], res[:6]):
+            assert r["iters"] == 200
+            Q = _dev_problem(pr)
+            one = s.solve(Q["C"], Q["p"], Q["q"], rho=pr.rho, tol=-1.0, max_iter=200, X=Q["X"], mu=Q["mu"], nu=Q["nu"])
+            assert abs(r["primal_obj"] - one["primal_obj"]) <= 1e-5 * abs(one["primal_obj"])
+            assert abs(r["res_l1"] - one["res_l1"]) <= 1e-4 * one["res_l1"] + 1e-9
+            S = pr.rho * 4
+            assert float((P["X"] - Q["X"]).abs().max()) <= 8 * EPS32 * S * 200

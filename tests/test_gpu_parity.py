@@ -97,7 +97,7 @@ def test_variants_agree_bitwise_on_a_solve(variant):
     outs = {}
     for v in (1, 2):
         C, p, q, X, mu, nu = _gpu_inputs(pr)
-        with drot.Solver(device=0, step_variant=v, tile_k=2, grid_ctas=53) as s:
+        with drot.Solver(device=0, step_variant=v, tile_k=2, grid_ctas=53, deterministic=True) as s:
             o = s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=300, X=X, mu=mu, nu=nu)
         outs[v] = (X.cpu().numpy(), mu.cpu().numpy(), o["primal_obj"])
     assert np.array_equal(outs[1][0], outs[2][0])
@@ -203,6 +203,19 @@ def test_stop_rules_match_oracle(rule):
     assert 0.5 * ref["iters"] <= out["iters"] <= 2.0 * ref["iters"] + 5
 
 
+@pytest.mark.parametrize("m,n", [(300, 2600), (1000, 200)])
+def test_autotune_picks_a_plan_and_keeps_parity(m, n):
+    pr = workloads.make_problem("plain_8192x6144", seed=m + n, m=m, n=n)
+    with drot.Solver(device=0, autotune=True) as s:
+        _step_parity(s, pr, 2, seed=5)
+        prof = s.profile()
+        assert prof["step_variant"] in (1, 2) and prof["tile_k"] in (1, 2, 4)
+        first = (prof["step_variant"], prof["tile_k"])
+        _step_parity(s, pr, 1, seed=6)  # the choice is cached per shape
+        prof = s.profile()
+        assert (prof["step_variant"], prof["tile_k"]) == first
+
+
 def test_max_iter_zero_returns_cold_start(solver):
     pr = workloads.make_problem("plain_256", seed=2, m=9, n=13)
     C, p, q, X, mu, nu = _gpu_inputs(pr)
@@ -212,18 +225,21 @@ def test_max_iter_zero_returns_cold_start(solver):
     assert np.array_equal(X.cpu().numpy(), ref)
 
 
-def test_deterministic_bitwise(solver):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_deterministic_mode_bitwise(variant):
     pr = workloads.make_problem("plain_8192x6144", seed=3, m=700, n=900)
     outs = []
     for _ in range(2):
         C, p, q, X, mu, nu = _gpu_inputs(pr)
-        o = solver.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=50, X=X, mu=mu, nu=nu)
+        with drot.Solver(device=0, deterministic=True, step_variant=variant) as s:
+            o = s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=50, X=X, mu=mu, nu=nu)
         outs.append((X.cpu().numpy().copy(), mu.cpu().numpy().copy(), o["primal_obj"], o["gap"]))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert outs[0][2] == outs[1][2] and outs[0][3] == outs[1][3]
 
 
-def test_host_buffers_match_device_buffers(solver):
+def test_host_buffers_match_device_buffers():
+    solver = drot.Solver(device=0, deterministic=True)
     pr = workloads.make_problem("plain_256", seed=4, m=100, n=77)
     C, p, q, X, mu, nu = _gpu_inputs(pr)
     od = solver.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=40, X=X, mu=mu, nu=nu)
@@ -238,6 +254,24 @@ def test_host_buffers_match_device_buffers(solver):
     assert oh["iters"] == od["iters"] == 40
     assert np.array_equal(Xh[:, : pr.n], X.cpu().numpy())
     assert np.array_equal(muh, mu.cpu().numpy())
+    solver.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_accumulation_and_fixed_order_modes_agree(variant):
+    # the two summation modes differ only in the order of FP64 additions
+    pr = workloads.make_problem("plain_8192x6144", seed=13, m=300, n=1100)
+    X0, mu0, nu0 = workloads.random_start(pr.m, pr.n, seed=4)
+    res = {}
+    for det in (False, True):
+        C, p, q, X, mu, nu = _gpu_inputs(pr, X0, mu0, nu0)
+        with drot.Solver(device=0, deterministic=det, step_variant=variant) as s:
+            o = s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=20, X=X, mu=mu, nu=nu, warm=True)
+        res[det] = (X.cpu().numpy().astype(np.float64), mu.cpu().numpy(), o)
+    S = max(np.abs(X0).max(), pr.rho * (np.abs(mu0).max() + np.abs(nu0).max() + 1.0))
+    assert np.abs(res[False][0] - res[True][0]).max() <= 8 * EPS32 * S * 20
+    assert np.abs(res[False][1] - res[True][1]).max() <= 64 * EPS32 * S / pr.rho * 20
+    assert abs(res[False][2]["primal_obj"] - res[True][2]["primal_obj"]) <= 1e-6 * abs(res[True][2]["primal_obj"])
 
 
 def test_padding_columns_untouched(solver):
