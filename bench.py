@@ -360,8 +360,8 @@ def main(argv=None):
     ap.add_argument("--stop", choices=["gap", "full"], default="gap")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default plan")
     ap.add_argument("--deterministic", action="store_true", help="fixed-order partial sums instead of atomics")
-    ap.add_argument("--step-variant", type=int, default=0, choices=[0, 1, 2],
-                    help="fused step: 1 register-fed, 2 TMA-fed, 0 library default")
+    ap.add_argument("--step-variant", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="fused step: 1 register-fed, 2 TMA-fed, 3 async-copy-fed, 0 library default")
     ap.add_argument("--max-iter", type=int, default=3_000_000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample-iters", type=int, default=8)

@@ -86,7 +86,8 @@ typedef struct {
     int grid_ctas;              /* CTAs of the fused step kernel; 0: automatic */
     int profile;                /* 1: time every fused-step launch with CUDA events (drot_get_profile) */
     int step_variant;           /* fused step: 1 register-fed (128-bit loads), 2 TMA-fed (bulk copies into a
-                                   shared-memory ring); 0: automatic */
+                                   shared-memory ring), 3 async-copy-fed (per-warp cp.async ring);
+                                   0: automatic */
     int deterministic;          /* 1: row/column sums as fixed-order FP64 partials (bitwise reproducible
                                    runs); 0 (default): FP64 atomic adds into the totals (faster; the
                                    summation order, hence the last bits, may vary between runs) */
@@ -188,6 +189,58 @@ drot_status drot_solve_batched(drot_handle *h, int32_t B, const drot_problem *pr
 drot_status drot_solve_static(int64_t m, int64_t n, const float *C, int64_t ld, const double *p,
                               const double *q, double rho, double tol, int64_t max_iter, float *X,
                               double *mu, double *nu, int warm, void *stream, drot_result *res);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper: the paper always starts from X_0 = p q^T).
+ * An MLP maps per-point features of each source point to its dual potential; the seed follows
+ * Lemma opt-rel (Appendix A.2): a primal-dual optimum (X*, mu*, nu*) gives the DR fixed point
+ * Y* = X* + rho (mu* 1^T + 1 nu*^T), so predicted duals enter drot_solve as mu_0, nu_0 (warm = 1).
+ *
+ * Network: 64 features -> 256 -> 256 -> 256 -> 1 with ReLU; FP32 parameters (one flat vector of
+ * DROT_MLP_PARAMS floats: W1[256x64] b1[256] W2[256x256] b2[256] W3[256x256] b3[256] W4[256] b4[1],
+ * weights row-major [out x in]) with BF16 copies for the matrix products, BF16 activations,
+ * FP32 accumulation, Adam updates.  Feature rows are BF16, DROT_MLP_FEATURES wide; see
+ * drot_mlp_features for their content.  All buffers are device memory of the network's device. */
+#define DROT_MLP_FEATURES 64
+#define DROT_MLP_WIDTH 256
+#define DROT_MLP_PARAMS (256 * 64 + 256 + 2 * (256 * 256 + 256) + 256 + 1)
+typedef struct drot_mlp drot_mlp;
+
+/* Create a network on `device` with all parameters zero (set them with drot_mlp_set_params). */
+drot_status drot_mlp_create(drot_mlp **net, int device);
+drot_status drot_mlp_destroy(drot_mlp *net);
+/* Copy DROT_MLP_PARAMS floats from / to host memory; setting resets the Adam state. */
+drot_status drot_mlp_set_params(drot_mlp *net, const float *params);
+drot_status drot_mlp_get_params(drot_mlp *net, float *params);
+
+/* Feature rows of the m source points of one problem, written to rows [row0, row0 + m) of `feat`
+ * (BF16, DROT_MLP_FEATURES per row).  xs: m x 2 and yt: n x 2 FP32 point coordinates in the unit
+ * square; p, q FP64 marginals.  Row content: x_i (2), m p_i, 4x4 histograms of both clouds
+ * weighted by their marginals (16 + 16), weighted means of both clouds (2 + 2), weighted
+ * variances and covariance of the target cloud (3), a constant 1, zeros. */
+drot_status drot_mlp_features(drot_mlp *net, int64_t m, int64_t n, const float *xs, const float *yt,
+                              const double *p, const double *q, void *feat, int64_t row0);
+
+/* out[r] = network(feat[r]) for `rows` rows (a multiple of 64). */
+drot_status drot_mlp_forward(drot_mlp *net, int64_t rows, const void *feat, float *out);
+
+/* One training step on `rows` feature rows (a multiple of 64) grouped into `nseg` problems by
+ * seg[r] in [0, nseg) (-1: padding row, ignored).  Loss (gauge invariant: a constant added to a
+ * problem's potentials does not change it): with e_r = out_r - target_r and ebar_s the
+ * weight-averaged e over problem s, L = (1/nseg) sum_s sum_{r in s} weight_r (e_r - ebar_s)^2.
+ * update != 0 applies one Adam step (lr; beta 0.9, 0.999; eps 1e-8).  loss (host, may be NULL)
+ * receives L; grad (host, may be NULL) receives the DROT_MLP_PARAMS gradient before the update. */
+drot_status drot_mlp_train_step(drot_mlp *net, int64_t rows, const void *feat, const float *target,
+                                const float *weight, const int32_t *seg, int32_t nseg, float lr, int update,
+                                float *loss, float *grad);
+
+/* Warm start for one problem: predicts the source potentials, centres them (p-weighted mean 0),
+ * divides by cost_scale (the factor by which the squared distances were divided to form C),
+ * sets nu_j = min_i (C_ij - mu_i) and then mu_i = min_j (C_ij - nu_j), so mu_i + nu_j <= C_ij;
+ * writes X = p q^T.  Pass X, mu, nu to drot_solve with warm = 1. */
+drot_status drot_mlp_warm_start(drot_mlp *net, int64_t m, int64_t n, const float *xs, const float *yt,
+                                const double *p, const double *q, double cost_scale, const float *C,
+                                int64_t ld, float *X, double *mu, double *nu);
 
 /* Release the handle and its workspace (NULL is accepted). */
 drot_status drot_destroy(drot_handle *h);

@@ -22,6 +22,7 @@
 #include "../../include/drot.h"
 #include "drot_kernels.cuh"
 #include "drot_batched.cuh"
+#include "drot_mlp.cuh"
 
 using drot::Scalars;
 
@@ -65,12 +66,24 @@ cudaError_t set_tma_attr() {
                                 (int)drot::TmaLayout<K, S>::bytes);
 }
 
-// Opt the TMA-fed kernels into their shared-memory ring size on the current device
+template <int K, int S>
+cudaError_t set_async_attr() {
+    return cudaFuncSetAttribute(drot::drot_step_async_kernel<K, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)drot::AsyncLayout<K, S>::bytes);
+}
+
+// Ring depth of the async-copy-fed step per tile width (two CTAs per SM).
+int async_stages(int K) { return K == 4 ? 3 : (K == 2 ? 4 : 6); }
+
+// Opt the ring-fed kernels into their shared-memory size on the current device
 // (done once per handle, outside any stream capture).
 cudaError_t set_kernel_attributes() {
     cudaError_t e = set_tma_attr<1, 8>();
     if (e == cudaSuccess) e = set_tma_attr<2, 4>();
     if (e == cudaSuccess) e = set_tma_attr<4, 4>();
+    if (e == cudaSuccess) e = set_async_attr<1, 6>();
+    if (e == cudaSuccess) e = set_async_attr<2, 4>();
+    if (e == cudaSuccess) e = set_async_attr<4, 3>();
     return e;
 }
 
@@ -83,6 +96,15 @@ int tma_occupancy() {
     return nb;
 }
 
+template <int K, int S>
+int async_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, drot::drot_step_async_kernel<K, S>, drot::kThreads,
+                                                      drot::AsyncLayout<K, S>::bytes) != cudaSuccess)
+        return -1;
+    return nb;
+}
+
 template <int K>
 int ldg_occupancy() {
     int nb = 0;
@@ -90,6 +112,12 @@ int ldg_occupancy() {
         cudaSuccess)
         return -1;
     return nb;
+}
+
+template <int K, int S>
+cudaError_t launch_async(int G, const drot::StepArgs &A, cudaStream_t s) {
+    drot::drot_step_async_kernel<K, S><<<G, drot::kThreads, drot::AsyncLayout<K, S>::bytes, s>>>(A);
+    return cudaGetLastError();
 }
 
 template <int K, int S>
@@ -128,7 +156,7 @@ struct drot_handle {
     drot_profile prof{};
     std::string last_error;
 
-    int occ[3][5] = {};  // resident CTAs per SM of the fused step [variant][K]
+    int occ[4][5] = {};  // resident CTAs per SM of the fused step [variant][K]
     struct Tuned {
         long long m, n;
         int variant, K;
@@ -146,10 +174,11 @@ struct drot_handle {
 
 namespace {
 cudaError_t fill_occupancy(drot_handle *h) {
-    const int v[3][5] = {{0, 0, 0, 0, 0},
+    const int v[4][5] = {{0, 0, 0, 0, 0},
                          {0, ldg_occupancy<1>(), ldg_occupancy<2>(), 0, ldg_occupancy<4>()},
-                         {0, tma_occupancy<1, 8>(), tma_occupancy<2, 4>(), 0, tma_occupancy<4, 4>()}};
-    for (int a = 0; a < 3; ++a)
+                         {0, tma_occupancy<1, 8>(), tma_occupancy<2, 4>(), 0, tma_occupancy<4, 4>()},
+                         {0, async_occupancy<1, 6>(), async_occupancy<2, 4>(), 0, async_occupancy<4, 3>()}};
+    for (int a = 0; a < 4; ++a)
         for (int k = 0; k < 5; ++k) {
             if (v[a][k] < 0) return cudaErrorUnknown;
             h->occ[a][k] = v[a][k];
@@ -216,7 +245,7 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
         for (const auto &t : h->tuned)
             if (t.m == m && t.n == n) {
                 if (K != 1 && K != 2 && K != 4) K = t.K;
-                if (variant != 1 && variant != 2) variant = t.variant;
+                if (variant < 1 || variant > 3) variant = t.variant;
             }
     }
     if (K != 1 && K != 2 && K != 4) {
@@ -228,9 +257,9 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
     P.TW = 128 * K;
     P.T = (int)((n + P.TW - 1) / P.TW);
     const long long units = (long long)P.T * m;
-    if (variant != 1 && variant != 2) variant = 1;
+    if (variant < 1 || variant > 3) variant = 1;
     P.variant = variant;
-    P.S = variant == 2 ? tma_stages(K) : 0;
+    P.S = variant == 2 ? tma_stages(K) : (variant == 3 ? async_stages(K) : 0);
     P.accumulate = h->cfg.deterministic ? 0 : 1;
     int G = h->cfg.grid_ctas;
     if (G <= 0) {
@@ -274,7 +303,8 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
         P.tile_slot[t] = first;
     }
     const long long mn = m + n;
-    P.fin_blocks = (int)std::min<long long>(2LL * h->num_sms, std::max<long long>(1, (mn + 255) / 256));
+    P.fin_blocks = (int)std::min<long long>(2LL * h->num_sms,
+                                            std::max<long long>(1, (mn + drot::kFinishThreads - 1) / drot::kFinishThreads));
 
     int gi = h->cfg.graph_iters;
     if (gi <= 0) {
@@ -385,11 +415,19 @@ drot::FinishArgs finish_args(const drot_handle *h, long long m, long long n, con
     F.G = P.G;
     F.inv_n = 1.0 / (double)n;
     F.inv_m = 1.0 / (double)m;
+    F.inv_mn = 1.0 / (double)(m + n);
     return F;
 }
 
 template <bool UPDATE>
 cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s) {
+    if (UPDATE && P.variant == 3) {
+        switch (P.K) {
+            case 1: return launch_async<1, 6>(P.G, A, s);
+            case 2: return launch_async<2, 4>(P.G, A, s);
+            default: return launch_async<4, 3>(P.G, A, s);
+        }
+    }
     if (UPDATE && P.variant == 2) {
         switch (P.K) {
             case 1: return launch_tma<1, 8>(P.G, A, s);
@@ -474,7 +512,7 @@ drot_status autotune_shape(drot_handle *h, long long m, long long n, long long l
     float best = 1e30f;
     int best_v = 1, best_k = 1;
     drot_status out = DROT_OK;
-    for (int variant = 1; variant <= 2 && out == DROT_OK; ++variant) {
+    for (int variant = 1; variant <= 3 && out == DROT_OK; ++variant) {
         for (int K : {1, 2, 4}) {
             if (K > 1 && n < 64LL * K) continue;  // a tile more than twice the row width leaves most lanes idle
             Plan P;
@@ -515,6 +553,7 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     Scalars &S = *h->h_sc;
     std::memset(&S, 0, sizeof S);
     S.rho = rho;
+    S.inv_rho = 1.0 / rho;
     S.tol = tol;
     S.max_iter = max_iter;
     S.stop_rule = (h->cfg.stop_rule & 7) ? (h->cfg.stop_rule & 7) : (DROT_STOP_GAP | DROT_STOP_RES_L1);
@@ -779,7 +818,8 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     int FB = 0;
     for (int b = 0; b < B; ++b) {
         const long long m = pr[b].m, n = pr[b].n;
-        const int fb = (int)std::min<long long>(32, std::max<long long>(1, (m + n + 255) / 256));
+        const int fb = (int)std::min<long long>(
+            64, std::max<long long>(1, (m + n + drot::kFinishThreads - 1) / drot::kFinishThreads));
         hp[b].fin_blocks = fb;
         FB += fb;
         off[b] = bytes;
@@ -847,6 +887,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     for (int b = 0; b < B; ++b) {
         std::memset(&hs[b], 0, sizeof(Scalars));
         hs[b].rho = pr[b].rho > 0.0 ? pr[b].rho : h->cfg.rho0 / (double)(pr[b].m + pr[b].n);
+        hs[b].inv_rho = 1.0 / hs[b].rho;
         hs[b].tol = tol;
         hs[b].max_iter = max_iter;
         hs[b].stop_rule = rule;
@@ -1346,6 +1387,7 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
     STATIC_CUDA(cudaMemcpyAsync(d_tile_slot, tile_slot, sizeof(int) * (T + 1), cudaMemcpyHostToDevice, stream));
     Scalars init{};
     init.rho = rho;
+    init.inv_rho = 1.0 / rho;
     init.tol = tol;
     init.max_iter = max_iter;
     init.stop_rule = DROT_STOP_GAP | DROT_STOP_RES_L1;
@@ -1377,6 +1419,7 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
     F.rowpart = rowpart; F.colpart = colpart; F.ctapart = ctapart; F.tile_slot = d_tile_slot;
     F.p = p; F.q = q; F.a = a_vec; F.b = b_vec; F.g = g_num; F.h = h_num; F.finpart = finpart; F.sc = sc;
     F.m = m; F.n = n; F.T = (int)T; F.TW = TW; F.G = G; F.inv_n = 1.0 / (double)n; F.inv_m = 1.0 / (double)m;
+    F.inv_mn = 1.0 / (double)(m + n);
 
     if (!warm) {
         const long long work = m * ((n + 3) / 4);
@@ -1436,3 +1479,292 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
     }
     return out;
 }
+
+// ---------------------------------------------------------------------------------------
+// Learned warm start (drot_mlp_*): an MLP from per-point features to dual potentials,
+// trained by the kernels of drot_mlp.cuh.  Parameters are one flat FP32 vector:
+// W1 [256 x 64] b1 [256] W2 [256 x 256] b2 [256] W3 [256 x 256] b3 [256] W4 [256] b4 [1].
+
+struct drot_mlp {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    float *w = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;  // DROT_MLP_PARAMS each
+    drot::mlp::bf16 *wb = nullptr;  // BF16 copies of W1, W2, W3
+    long long rows_cap = 0;
+    drot::mlp::bf16 *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *D = nullptr, *D2 = nullptr;
+    float *out = nullptr, *g = nullptr, *ebar = nullptr, *wsum = nullptr, *loss = nullptr;
+    int seg_cap = 0;
+    long long step = 0;
+    drot::mlp::bf16 *feat = nullptr;  // warm-start feature rows
+    long long feat_cap = 0;
+    float *pred = nullptr;
+};
+
+namespace {
+
+namespace M = drot::mlp;
+constexpr long long kW1 = (long long)M::kWidth * M::kIn, kB1 = M::kWidth;
+constexpr long long kW2 = (long long)M::kWidth * M::kWidth, kB2 = M::kWidth;
+constexpr long long kW3 = kW2, kB3 = M::kWidth, kW4 = M::kWidth, kB4 = 1;
+constexpr long long kOffW1 = 0, kOffB1 = kOffW1 + kW1, kOffW2 = kOffB1 + kB1, kOffB2 = kOffW2 + kW2;
+constexpr long long kOffW3 = kOffB2 + kB2, kOffB3 = kOffW3 + kW3, kOffW4 = kOffB3 + kB3, kOffB4 = kOffW4 + kW4;
+constexpr long long kParams = kOffB4 + kB4;
+static_assert(kParams == DROT_MLP_PARAMS, "parameter layout");
+// BF16 copies: W1, W2, W3 back to back
+constexpr long long kBfW1 = 0, kBfW2 = kW1, kBfW3 = kW1 + kW2, kBfCount = kW1 + kW2 + kW3;
+
+#define MLP_CUDA(call)                                    \
+    do {                                                  \
+        if ((call) != cudaSuccess) return DROT_ERR_CUDA;  \
+    } while (0)
+
+drot_status mlp_reserve(drot_mlp *net, long long rows, int nseg) {
+    if (rows > net->rows_cap) {
+        void *bufs[] = {net->H1, net->H2, net->H3, net->D, net->D2, net->out, net->g};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        const size_t hb = sizeof(M::bf16) * (size_t)rows * M::kWidth;
+        if (cudaMalloc(&net->H1, hb) != cudaSuccess || cudaMalloc(&net->H2, hb) != cudaSuccess ||
+            cudaMalloc(&net->H3, hb) != cudaSuccess || cudaMalloc(&net->D, hb) != cudaSuccess ||
+            cudaMalloc(&net->D2, hb) != cudaSuccess || cudaMalloc(&net->out, sizeof(float) * rows) != cudaSuccess ||
+            cudaMalloc(&net->g, sizeof(float) * rows) != cudaSuccess) {
+            net->rows_cap = 0;
+            return DROT_ERR_OOM;
+        }
+        net->rows_cap = rows;
+    }
+    if (nseg > net->seg_cap) {
+        if (net->ebar) cudaFree(net->ebar);
+        if (net->wsum) cudaFree(net->wsum);
+        if (cudaMalloc(&net->ebar, sizeof(float) * nseg) != cudaSuccess ||
+            cudaMalloc(&net->wsum, sizeof(float) * nseg) != cudaSuccess)
+            return DROT_ERR_OOM;
+        net->seg_cap = nseg;
+    }
+    return DROT_OK;
+}
+
+template <bool TA, bool TB>
+cudaError_t mlp_gemm(cudaStream_t s, const M::bf16 *A, const M::bf16 *B, int Mr, int Nc, int K, int lda, int ldb,
+                     int epi, float *Cf, M::bf16 *Cb, int ldc, const float *bias, const M::bf16 *mask, int ksplit) {
+    const int tiles = (Mr / 32) * (Nc / 32);
+    dim3 grid((tiles + 3) / 4, 1, ksplit);
+    M::gemm_kernel<TA, TB><<<grid, 128, 0, s>>>(A, B, Mr, Nc, K, lda, ldb, epi, Cf, Cb, ldc, bias, mask);
+    return cudaGetLastError();
+}
+
+// Forward pass over `rows` feature rows (a multiple of 64): out[r].
+drot_status mlp_forward(drot_mlp *net, long long rows, const M::bf16 *F) {
+    cudaStream_t s = net->stream;
+    const int R = (int)rows;
+    MLP_CUDA((mlp_gemm<false, true>(s, F, net->wb + kBfW1, R, M::kWidth, M::kIn, M::kIn, M::kIn, M::kReluBiasBf16,
+                                    nullptr, net->H1, M::kWidth, net->w + kOffB1, nullptr, 1)));
+    MLP_CUDA((mlp_gemm<false, true>(s, net->H1, net->wb + kBfW2, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
+                                    M::kReluBiasBf16, nullptr, net->H2, M::kWidth, net->w + kOffB2, nullptr, 1)));
+    MLP_CUDA((mlp_gemm<false, true>(s, net->H2, net->wb + kBfW3, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
+                                    M::kReluBiasBf16, nullptr, net->H3, M::kWidth, net->w + kOffB3, nullptr, 1)));
+    M::output_kernel<<<(R + 7) / 8, 256, 0, s>>>(net->H3, net->w + kOffW4, net->w + kOffB4, net->out, rows);
+    MLP_CUDA(cudaGetLastError());
+    return DROT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+drot_status drot_mlp_create(drot_mlp **out, int device) {
+    if (!out) return DROT_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DROT_ERR_CUDA;
+    }
+    drot_mlp *net = new (std::nothrow) drot_mlp();
+    if (!net) return DROT_ERR_OOM;
+    net->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete net;
+        return DROT_ERR_CUDA;
+    }
+    const size_t pb = sizeof(float) * kParams;
+    if (cudaMalloc(&net->w, pb) != cudaSuccess || cudaMalloc(&net->grad, pb) != cudaSuccess ||
+        cudaMalloc(&net->m1, pb) != cudaSuccess || cudaMalloc(&net->m2, pb) != cudaSuccess ||
+        cudaMalloc(&net->wb, sizeof(M::bf16) * kBfCount) != cudaSuccess ||
+        cudaMalloc(&net->loss, sizeof(float)) != cudaSuccess) {
+        drot_mlp_destroy(net);
+        return DROT_ERR_OOM;
+    }
+    cudaMemsetAsync(net->w, 0, pb, net->stream);
+    cudaMemsetAsync(net->m1, 0, pb, net->stream);
+    cudaMemsetAsync(net->m2, 0, pb, net->stream);
+    cudaMemsetAsync(net->wb, 0, sizeof(M::bf16) * kBfCount, net->stream);
+    if (cudaStreamSynchronize(net->stream) != cudaSuccess) {
+        drot_mlp_destroy(net);
+        return DROT_ERR_CUDA;
+    }
+    *out = net;
+    return DROT_OK;
+}
+
+drot_status drot_mlp_destroy(drot_mlp *net) {
+    if (!net) return DROT_OK;
+    cudaSetDevice(net->device);
+    if (net->stream) cudaStreamSynchronize(net->stream);
+    void *bufs[] = {net->w, net->grad, net->m1, net->m2, net->wb, net->H1, net->H2, net->H3, net->D, net->D2,
+                    net->out, net->g, net->ebar, net->wsum, net->loss, net->feat, net->pred};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (net->stream) cudaStreamDestroy(net->stream);
+    delete net;
+    return DROT_OK;
+}
+
+drot_status drot_mlp_set_params(drot_mlp *net, const float *params) {
+    if (!net || !params) return DROT_ERR_INVALID_ARG;
+    cudaSetDevice(net->device);
+    cudaStream_t s = net->stream;
+    const size_t pb = sizeof(float) * kParams;
+    MLP_CUDA(cudaMemcpyAsync(net->w, params, pb, cudaMemcpyHostToDevice, s));
+    MLP_CUDA(cudaMemsetAsync(net->m1, 0, pb, s));
+    MLP_CUDA(cudaMemsetAsync(net->m2, 0, pb, s));
+    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW1, net->wb + kBfW1, kW1);
+    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW2, net->wb + kBfW2, kW2);
+    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW3, net->wb + kBfW3, kW3);
+    MLP_CUDA(cudaGetLastError());
+    net->step = 0;
+    MLP_CUDA(cudaStreamSynchronize(s));
+    return DROT_OK;
+}
+
+drot_status drot_mlp_get_params(drot_mlp *net, float *params) {
+    if (!net || !params) return DROT_ERR_INVALID_ARG;
+    cudaSetDevice(net->device);
+    MLP_CUDA(cudaMemcpyAsync(params, net->w, sizeof(float) * kParams, cudaMemcpyDeviceToHost, net->stream));
+    MLP_CUDA(cudaStreamSynchronize(net->stream));
+    return DROT_OK;
+}
+
+drot_status drot_mlp_features(drot_mlp *net, int64_t m, int64_t n, const float *xs, const float *yt,
+                              const double *p, const double *q, void *feat, int64_t row0) {
+    if (!net || m < 1 || n < 1 || !xs || !yt || !p || !q || !feat || row0 < 0) return DROT_ERR_INVALID_ARG;
+    cudaSetDevice(net->device);
+    M::features_kernel<<<1, 256, 0, net->stream>>>(xs, yt, p, q, m, n, static_cast<M::bf16 *>(feat), row0);
+    MLP_CUDA(cudaGetLastError());
+    MLP_CUDA(cudaStreamSynchronize(net->stream));
+    return DROT_OK;
+}
+
+drot_status drot_mlp_forward(drot_mlp *net, int64_t rows, const void *feat, float *out) {
+    if (!net || rows < 64 || rows % 64 != 0 || !feat || !out) return DROT_ERR_INVALID_ARG;
+    cudaSetDevice(net->device);
+    drot_status st = mlp_reserve(net, rows, 1);
+    if (st != DROT_OK) return st;
+    st = mlp_forward(net, rows, static_cast<const M::bf16 *>(feat));
+    if (st != DROT_OK) return st;
+    MLP_CUDA(cudaMemcpyAsync(out, net->out, sizeof(float) * rows, cudaMemcpyDeviceToDevice, net->stream));
+    MLP_CUDA(cudaStreamSynchronize(net->stream));
+    return DROT_OK;
+}
+
+drot_status drot_mlp_train_step(drot_mlp *net, int64_t rows, const void *feat, const float *target,
+                                const float *weight, const int32_t *seg, int32_t nseg, float lr, int update,
+                                float *loss, float *grad) {
+    if (!net || rows < 64 || rows % 64 != 0 || !feat || !target || !weight || !seg || nseg < 1)
+        return DROT_ERR_INVALID_ARG;
+    cudaSetDevice(net->device);
+    drot_status st = mlp_reserve(net, rows, nseg);
+    if (st != DROT_OK) return st;
+    cudaStream_t s = net->stream;
+    const M::bf16 *F = static_cast<const M::bf16 *>(feat);
+    st = mlp_forward(net, rows, F);
+    if (st != DROT_OK) return st;
+    const int R = (int)rows;
+    MLP_CUDA(cudaMemsetAsync(net->grad, 0, sizeof(float) * kParams, s));
+    MLP_CUDA(cudaMemsetAsync(net->ebar, 0, sizeof(float) * nseg, s));
+    MLP_CUDA(cudaMemsetAsync(net->wsum, 0, sizeof(float) * nseg, s));
+    MLP_CUDA(cudaMemsetAsync(net->loss, 0, sizeof(float), s));
+    M::loss_pass1_kernel<<<256, 256, 0, s>>>(net->out, target, weight, seg, rows, net->ebar, net->wsum);
+    M::loss_pass2_kernel<<<256, 256, 0, s>>>(net->out, target, weight, seg, rows, net->ebar, net->wsum,
+                                             1.f / (float)nseg, net->g, net->loss);
+    // layer 4 and the gradient at the output of layer 3 (through its ReLU)
+    M::output_backward_kernel<<<R / 64, M::kWidth, 0, s>>>(net->g, net->H3, net->w + kOffW4, rows,
+                                                           net->grad + kOffW4, net->grad + kOffB4, net->D);
+    MLP_CUDA(cudaGetLastError());
+    const int ks = std::max(1, std::min(64, R / 256));
+    // layer 3: dW3 = D3^T H2, db3 = colsum D3, D2 = (D3 W3) o (H2 > 0)
+    MLP_CUDA((mlp_gemm<true, false>(s, net->D, net->H2, M::kWidth, M::kWidth, R, M::kWidth, M::kWidth, M::kAtomicF32,
+                                    net->grad + kOffW3, nullptr, M::kWidth, nullptr, nullptr, ks)));
+    M::column_sum_kernel<<<R / 64, M::kWidth, 0, s>>>(net->D, rows, net->grad + kOffB3);
+    MLP_CUDA((mlp_gemm<false, false>(s, net->D, net->wb + kBfW3, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
+                                     M::kMaskBf16, nullptr, net->D2, M::kWidth, nullptr, net->H2, 1)));
+    // layer 2: dW2 = D2^T H1, db2, D1 = (D2 W2) o (H1 > 0)  (D1 reuses D)
+    MLP_CUDA((mlp_gemm<true, false>(s, net->D2, net->H1, M::kWidth, M::kWidth, R, M::kWidth, M::kWidth,
+                                    M::kAtomicF32, net->grad + kOffW2, nullptr, M::kWidth, nullptr, nullptr, ks)));
+    M::column_sum_kernel<<<R / 64, M::kWidth, 0, s>>>(net->D2, rows, net->grad + kOffB2);
+    MLP_CUDA((mlp_gemm<false, false>(s, net->D2, net->wb + kBfW2, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
+                                     M::kMaskBf16, nullptr, net->D, M::kWidth, nullptr, net->H1, 1)));
+    // layer 1: dW1 = D1^T F, db1
+    MLP_CUDA((mlp_gemm<true, false>(s, net->D, F, M::kWidth, M::kIn, R, M::kWidth, M::kIn, M::kAtomicF32,
+                                    net->grad + kOffW1, nullptr, M::kIn, nullptr, nullptr, ks)));
+    M::column_sum_kernel<<<R / 64, M::kWidth, 0, s>>>(net->D, rows, net->grad + kOffB1);
+    MLP_CUDA(cudaGetLastError());
+    if (update) {
+        net->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+        struct Seg { long long off, cnt, bf; } segs[] = {
+            {kOffW1, kW1, kBfW1}, {kOffB1, kB1, -1}, {kOffW2, kW2, kBfW2}, {kOffB2, kB2, -1},
+            {kOffW3, kW3, kBfW3}, {kOffB3, kB3, -1}, {kOffW4, kW4 + kB4, -1}};
+        for (const Seg &g : segs)
+            M::adam_kernel<<<64, 256, 0, s>>>(net->w + g.off, net->grad + g.off, net->m1 + g.off, net->m2 + g.off,
+                                              g.bf >= 0 ? net->wb + g.bf : nullptr, g.cnt, lr, b1, b2, 1e-8f, c1, c2);
+        MLP_CUDA(cudaGetLastError());
+    }
+    if (loss) MLP_CUDA(cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (grad) MLP_CUDA(cudaMemcpyAsync(grad, net->grad, sizeof(float) * kParams, cudaMemcpyDeviceToHost, s));
+    MLP_CUDA(cudaStreamSynchronize(s));
+    return DROT_OK;
+}
+
+drot_status drot_mlp_warm_start(drot_mlp *net, int64_t m, int64_t n, const float *xs, const float *yt,
+                                const double *p, const double *q, double cost_scale, const float *C, int64_t ld,
+                                float *X, double *mu, double *nu) {
+    if (!net || m < 1 || n < 1 || !xs || !yt || !p || !q || !C || !X || !mu || !nu || ld < n || ld % 4 != 0 ||
+        !(cost_scale > 0.0))
+        return DROT_ERR_INVALID_ARG;
+    cudaSetDevice(net->device);
+    cudaStream_t s = net->stream;
+    const long long rows = (m + 63) / 64 * 64;
+    if (rows > net->feat_cap) {
+        if (net->feat) cudaFree(net->feat);
+        if (net->pred) cudaFree(net->pred);
+        net->feat = nullptr;
+        net->pred = nullptr;
+        net->feat_cap = 0;
+        if (cudaMalloc(&net->feat, sizeof(M::bf16) * rows * M::kIn) != cudaSuccess ||
+            cudaMalloc(&net->pred, sizeof(float) * rows) != cudaSuccess)
+            return DROT_ERR_OOM;
+        net->feat_cap = rows;
+    }
+    drot_status st = mlp_reserve(net, rows, 1);
+    if (st != DROT_OK) return st;
+    MLP_CUDA(cudaMemsetAsync(net->feat, 0, sizeof(M::bf16) * rows * M::kIn, s));
+    M::features_kernel<<<1, 256, 0, s>>>(xs, yt, p, q, m, n, net->feat, 0);
+    MLP_CUDA(cudaGetLastError());
+    st = mlp_forward(net, rows, net->feat);
+    if (st != DROT_OK) return st;
+    // centred prediction in units of C, then the c-transforms (exact dual feasibility)
+    M::centre_prediction_kernel<<<1, 1024, 0, s>>>(net->out, p, m, 1.0 / cost_scale, mu);
+    M::c_transform_cols_kernel<<<(int)std::max<long long>(1, (n + 127) / 128), 128, 0, s>>>(C, m, n, ld, mu, nu);
+    M::c_transform_rows_kernel<<<(int)std::max<long long>(1, (m + 7) / 8), 256, 0, s>>>(C, m, n, ld, nu, mu);
+    // X_0 = p q^T (Sec. 4)
+    const long long work = m * ((n + 3) / 4);
+    drot::drot_init_plan_kernel<<<(int)std::min<long long>(1184, std::max<long long>(1, (work + 255) / 256)), 256, 0,
+                                  s>>>(X, p, q, m, n, ld);
+    MLP_CUDA(cudaGetLastError());
+    MLP_CUDA(cudaStreamSynchronize(s));
+    return DROT_OK;
+}
+
+}  // extern "C"

@@ -70,6 +70,7 @@ __device__ __forceinline__ FinishArgs batch_finish_args(const BatchProb& P) {
     F.n = P.n;
     F.inv_n = P.inv_n;
     F.inv_m = P.inv_m;
+    F.inv_mn = 1.0 / (double)(P.m + P.n);
     return F;
 }
 

@@ -41,7 +41,9 @@ namespace drot {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kFlushRows = 16;  // rows per warp between FP32 -> FP64 promotions
-constexpr int kFinishThreads = 256;
+// Finish blocks are small so that the O(m + n) FP64 work (B300's FP64 rate is a
+// small fraction of its FP32 rate) spreads over every SM.
+constexpr int kFinishThreads = 64;
 constexpr int kFinishAcc = 6;
 
 enum DoneCode : int { kRunning = 0, kConverged = 1, kIterCap = 2, kNonFinite = 3, kFault = 4 };
@@ -51,6 +53,7 @@ struct Scalars {
     double c;              // scalar term of phi_k, psi_k (see above)
     double alpha;          // alpha_k
     double rho;
+    double inv_rho;        // 1 / rho (set with rho; avoids FP64 divisions on the device)
     double tol;
     double sum_p, sum_q;
     double min_p, min_q;
@@ -562,6 +565,195 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
     }
 }
 
+
+// ------------------------------------------------------------ async-copy-fed variant
+//
+// Same arithmetic, partials and work split as drot_step_kernel<K, true>.  Each warp
+// streams its own rows through a private S-stage ring in shared memory filled with
+// 16-byte cp.async copies: while a warp computes row r, the copies of its next S-1
+// rows are in flight, and they occupy shared memory, not registers.  Every lane
+// reads back only the 16-byte chunks it copied itself, so a lane's own
+// cp.async.wait_group is the only synchronisation the ring needs.  Column partials
+// are promoted to FP64 in registers; the ring is reused as the cross-warp
+// reduction buffer at the end of each column tile.
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int K, int S>
+struct AsyncLayout {
+    static constexpr int TW = 128 * K;
+    static constexpr size_t ring_floats = (size_t)kWarps * S * 2 * TW;  // X and C per stage
+    static constexpr size_t bytes = ring_floats * sizeof(float) > (size_t)kWarps * TW * sizeof(double)
+                                        ? ring_floats * sizeof(float)
+                                        : (size_t)kWarps * TW * sizeof(double);
+};
+
+template <int K, int S>
+__global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A) {
+    constexpr int TW = 128 * K;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* ring = reinterpret_cast<float*>(smem_raw) + (size_t)(threadIdx.x >> 5) * S * 2 * TW;
+    double* s_col = reinterpret_cast<double*>(smem_raw);  // reused at the end of each tile
+    __shared__ double s_red[kWarps][2];
+
+    if (A.sc->done != kRunning) return;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long m = A.m, n = A.n, ld = A.ld;
+    const long long w0 = A.wbound[blockIdx.x];
+    const long long w1 = A.wbound[blockIdx.x + 1];
+    const float rho = (float)A.sc->rho;
+    const double cs = A.sc->c;
+    int slot = A.slot_base[blockIdx.x];
+    double scx64 = 0.0, sd64 = 0.0;
+
+    long long w = w0;
+    while (w < w1) {
+        const long long t = w / m;
+        const long long seg_end = min(w1, (t + 1) * m);
+        const long long i0 = w - t * m, i1 = seg_end - t * m;
+        const long long col0 = t * TW;
+
+        float psi[K][4], cacc[K][4];
+        double cacc64[K][4];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const long long j = col0 + kk * 128 + lane * 4 + e;
+                psi[kk][e] = j < n ? (float)((A.h[j] + cs) * A.inv_m) : 0.f;
+                cacc[kk][e] = 0.f;
+                cacc64[kk][e] = 0.0;
+            }
+        // rows of this warp in the tile: i0 + warp + kWarps * r, r = 0 .. nr-1
+        const long long first = i0 + warp;
+        const int nr = first < i1 ? (int)((i1 - 1 - first) / kWarps + 1) : 0;
+        auto issue = [&](int r) {
+            if (r < nr) {
+                const long long i = first + (long long)kWarps * r;
+                float* xs = ring + (size_t)(r % S) * 2 * TW;
+                float* cs_ = xs + TW;
+                const long long rowoff = i * ld + col0 + lane * 4;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    if (col0 + kk * 128 + lane * 4 < n) {
+                        cp_async16(xs + kk * 128 + lane * 4, A.X + rowoff + kk * 128);
+                        cp_async16(cs_ + kk * 128 + lane * 4, A.C + rowoff + kk * 128);
+                    }
+                }
+            }
+            cp_async_commit();  // an empty group keeps the group count in step
+        };
+#pragma unroll
+        for (int r = 0; r < S - 1; ++r) issue(r);
+
+        float scx = 0.f, sd = 0.f;
+        int since_flush = 0;
+        for (int r = 0; r < nr; ++r) {
+            issue(r + S - 1);
+            cp_async_wait<S - 1>();
+            const long long i = first + (long long)kWarps * r;
+            const float* xs = ring + (size_t)(r % S) * 2 * TW;
+            const float* csr = xs + TW;
+            const float phi = (float)((A.g[i] + cs) * A.inv_n);
+            float* dst_row = A.X + i * ld + col0;
+            float rs = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const int jl = kk * 128 + lane * 4;
+                const long long j = col0 + jl;
+                if (j < n) {
+                    const float4 xv = *reinterpret_cast<const float4*>(xs + jl);
+                    const float4 cv = *reinterpret_cast<const float4*>(csr + jl);
+                    float x4[4] = {xv.x, xv.y, xv.z, xv.w};
+                    const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (j + e < n) {
+                            const float d = fmaf(-rho, cc[e], phi + psi[kk][e]);
+                            const float xn = fmaxf(x4[e] + d, 0.f);
+                            scx = fmaf(cc[e], xn, scx);
+                            const float dp = fmaxf(d, 0.f);
+                            sd = fmaf(dp, dp, sd);
+                            x4[e] = xn;
+                            rs += xn;
+                            cacc[kk][e] += xn;
+                        }
+                    }
+                    if (j + 3 < n) {
+                        *reinterpret_cast<float4*>(dst_row + jl) = make_float4(x4[0], x4[1], x4[2], x4[3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (j + e < n) dst_row[jl + e] = x4[e];
+                    }
+                }
+            }
+            rs = warp_sum_f32(rs);
+            if (lane == 0) {
+                if (A.accumulate) atomicAdd(A.u + i, (double)rs);
+                else A.rowpart[t * m + i] = (double)rs;
+            }
+            if (++since_flush == kFlushRows) {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        cacc64[kk][e] += (double)cacc[kk][e];
+                        cacc[kk][e] = 0.f;
+                    }
+                scx64 += (double)scx;
+                sd64 += (double)sd;
+                scx = 0.f;
+                sd = 0.f;
+                since_flush = 0;
+            }
+        }
+        cp_async_wait<0>();
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) cacc64[kk][e] += (double)cacc[kk][e];
+        scx64 += (double)scx;
+        sd64 += (double)sd;
+        __syncthreads();  // every warp is done with its ring: reuse it for the column reduction
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) s_col[(size_t)warp * TW + kk * 128 + lane * 4 + e] = cacc64[kk][e];
+        __syncthreads();
+        double* out = A.colpart + (long long)slot * TW;
+        for (int x = threadIdx.x; x < TW; x += kThreads) {
+            double v = 0.0;
+#pragma unroll
+            for (int wv = 0; wv < kWarps; ++wv) v += s_col[(size_t)wv * TW + x];
+            if (!A.accumulate) out[x] = v;
+            else if (col0 + x < n) atomicAdd(A.v + col0 + x, v);
+        }
+        __syncthreads();
+        ++slot;
+        w = seg_end;
+    }
+
+    double v[2] = {scx64, sd64};
+    block_sum_f64<2, kThreads>(v, s_red);
+    if (threadIdx.x == 0) {
+        if (A.accumulate) {
+            atomicAdd(A.acc + 0, v[0]);
+            atomicAdd(A.acc + 1, v[1]);
+        } else {
+            A.ctapart[2 * blockIdx.x + 0] = v[0];
+            A.ctapart[2 * blockIdx.x + 1] = v[1];
+        }
+    }
+}
+
 struct FinishArgs {
     const double* rowpart;
     const double* colpart;
@@ -582,6 +774,7 @@ struct FinishArgs {
     long long m, n;
     int T, TW, G;
     double inv_n, inv_m;
+    double inv_mn;          // 1 / (m + n)
 };
 
 // Sum of `count` partials spaced `stride` apart, in a fixed order: four
@@ -707,18 +900,17 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
     __shared__ double s_red2[kFinishThreads / 32][kFinishAcc + 2];
     block_sum_f64<kFinishAcc + 2, kFinishThreads>(tot, s_red2);
     if (threadIdx.x == 0) {
-        const double mnd = (double)(A.m + A.n);
-        const double beta = tot[0] / mnd;                  // step 5
+        const double beta = tot[0] * A.inv_mn;            // step 5
         const double c_new = 2.0 * beta - sc->alpha;       // steps 6-7 scalar term
         const double pphi = (tot[3] + c_new * sc->sum_p) * A.inv_n;
         const double qpsi = (tot[4] + c_new * sc->sum_q) * A.inv_m;
-        const double rho = sc->rho;
+        const double inv_rho = sc->inv_rho;
         const double primal = tot[kFinishAcc + 0];
-        const double dual = (pphi + qpsi) / rho;
+        const double dual = (pphi + qpsi) * inv_rho;
         const double gap = fabs(primal - dual);
         const double res_l1 = tot[1];
         const double res_l2 = sqrt(tot[2]);
-        const double dres = sqrt(tot[kFinishAcc + 1]) / rho;
+        const double dres = sqrt(tot[kFinishAcc + 1]) * inv_rho;
         sc->alpha -= beta;                                 // step 8
         sc->c = c_new;
         sc->beta = beta;
@@ -838,7 +1030,7 @@ __device__ __forceinline__ void init_state_body(const FinishArgs& A, const doubl
     __shared__ double s_red2[kFinishThreads / 32][1];
     block_sum_f64<1, kFinishThreads>(tot, s_red2);
     if (threadIdx.x == 0) {
-        sc->alpha = tot[0] / (md + nd);
+        sc->alpha = tot[0] * A.inv_mn;
         sc->c = 0.0;
         sc->k = 0;
         sc->counter = 0u;

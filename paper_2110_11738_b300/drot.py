@@ -40,7 +40,13 @@ STATUS_NAMES = {
 # Every symbol include/drot.h declares.
 EXPORTED = ("drot_config_default", "drot_create", "drot_solve", "drot_solve_batched", "drot_destroy",
             "drot_get_profile", "drot_reset_profile", "drot_status_string", "drot_last_error",
-            "drot_solve_static")
+            "drot_solve_static", "drot_mlp_create", "drot_mlp_destroy", "drot_mlp_set_params",
+            "drot_mlp_get_params", "drot_mlp_features", "drot_mlp_forward", "drot_mlp_train_step",
+            "drot_mlp_warm_start")
+
+MLP_FEATURES = 64
+MLP_WIDTH = 256
+MLP_PARAMS = 256 * 64 + 256 + 2 * (256 * 256 + 256) + 256 + 1
 
 
 class DrotConfig(ctypes.Structure):
@@ -117,6 +123,24 @@ def load(build_if_missing: bool = True):
     lib.drot_status_string.argtypes = [ctypes.c_int]
     lib.drot_last_error.restype = ctypes.c_char_p
     lib.drot_last_error.argtypes = [vp]
+    f32p = ctypes.POINTER(ctypes.c_float)
+    lib.drot_mlp_create.restype = ctypes.c_int
+    lib.drot_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.drot_mlp_destroy.restype = ctypes.c_int
+    lib.drot_mlp_destroy.argtypes = [vp]
+    lib.drot_mlp_set_params.restype = ctypes.c_int
+    lib.drot_mlp_set_params.argtypes = [vp, f32p]
+    lib.drot_mlp_get_params.restype = ctypes.c_int
+    lib.drot_mlp_get_params.argtypes = [vp, f32p]
+    lib.drot_mlp_features.restype = ctypes.c_int
+    lib.drot_mlp_features.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, i64]
+    lib.drot_mlp_forward.restype = ctypes.c_int
+    lib.drot_mlp_forward.argtypes = [vp, i64, vp, vp]
+    lib.drot_mlp_train_step.restype = ctypes.c_int
+    lib.drot_mlp_train_step.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.c_int32, ctypes.c_float, ctypes.c_int,
+                                        f32p, f32p]
+    lib.drot_mlp_warm_start.restype = ctypes.c_int
+    lib.drot_mlp_warm_start.argtypes = [vp, i64, i64, vp, vp, vp, vp, ctypes.c_double, vp, i64, vp, vp, vp]
     lib.drot_solve_static.restype = ctypes.c_int
     lib.drot_solve_static.argtypes = [i64, i64, vp, i64, vp, vp, ctypes.c_double, ctypes.c_double, i64, vp, vp, vp,
                                       ctypes.c_int, vp, ctypes.POINTER(DrotResult)]
@@ -350,3 +374,88 @@ def padded_matrix(A, ld: Optional[int] = None, device=None):
     buf = torch.zeros((m, ld), dtype=torch.float32, device=device if device is not None else A.device)
     buf[:, :n] = A.to(buf.device)
     return buf[:, :n]
+
+
+# ---------------------------------------------------------------- learned warm start
+
+class Mlp:
+    """The warm-start network (drot_mlp_* in include/drot.h) on one GPU.
+
+    Feature matrices are torch.bfloat16 CUDA tensors of shape (rows, MLP_FEATURES) with
+    rows a multiple of 64; targets, weights are float32, seg int32 (-1 marks padding rows).
+    """
+
+    def __init__(self, device: int = 0, params: Optional[np.ndarray] = None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the warm-start network needs a CUDA device")
+        self.lib = load()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        st = self.lib.drot_mlp_create(ctypes.byref(h), self.device)
+        if st != DROT_OK:
+            raise DrotError(st, "drot_mlp_create")
+        self.handle = h.value
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if self.handle:
+            self.lib.drot_mlp_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != DROT_OK:
+            raise DrotError(st, what)
+
+    def set_params(self, params: np.ndarray) -> None:
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        assert a.size == MLP_PARAMS
+        self._check(self.lib.drot_mlp_set_params(ctypes.c_void_p(self.handle),
+                                                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(self.lib.drot_mlp_get_params(ctypes.c_void_p(self.handle),
+                                                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "get_params")
+        return a
+
+    def features(self, xs, yt, p, q, feat, row0: int = 0) -> None:
+        m, n = int(xs.shape[0]), int(yt.shape[0])
+        self._check(self.lib.drot_mlp_features(ctypes.c_void_p(self.handle), m, n, ctypes.c_void_p(_ptr(xs)),
+                                               ctypes.c_void_p(_ptr(yt)), ctypes.c_void_p(_ptr(p)),
+                                               ctypes.c_void_p(_ptr(q)), ctypes.c_void_p(_ptr(feat)), int(row0)),
+                    "features")
+
+    def forward(self, feat, out) -> None:
+        self._check(self.lib.drot_mlp_forward(ctypes.c_void_p(self.handle), int(feat.shape[0]),
+                                              ctypes.c_void_p(_ptr(feat)), ctypes.c_void_p(_ptr(out))), "forward")
+
+    def train_step(self, feat, target, weight, seg, nseg: int, lr: float, update: bool = True,
+                   want_grad: bool = False):
+        loss = ctypes.c_float(0.0)
+        grad = np.zeros(MLP_PARAMS, dtype=np.float32) if want_grad else None
+        st = self.lib.drot_mlp_train_step(ctypes.c_void_p(self.handle), int(feat.shape[0]),
+                                          ctypes.c_void_p(_ptr(feat)), ctypes.c_void_p(_ptr(target)),
+                                          ctypes.c_void_p(_ptr(weight)), ctypes.c_void_p(_ptr(seg)), int(nseg),
+                                          float(lr), int(bool(update)), ctypes.byref(loss),
+                                          grad.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+                                          if grad is not None else None)
+        self._check(st, "train_step")
+        return (loss.value, grad) if want_grad else loss.value
+
+    def warm_start(self, xs, yt, p, q, cost_scale: float, C, X, mu, nu) -> None:
+        m, n = int(xs.shape[0]), int(yt.shape[0])
+        st = self.lib.drot_mlp_warm_start(ctypes.c_void_p(self.handle), m, n, ctypes.c_void_p(_ptr(xs)),
+                                          ctypes.c_void_p(_ptr(yt)), ctypes.c_void_p(_ptr(p)),
+                                          ctypes.c_void_p(_ptr(q)), float(cost_scale), ctypes.c_void_p(_ptr(C)),
+                                          _ld_of(C), ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(mu)),
+                                          ctypes.c_void_p(_ptr(nu)))
+        self._check(st, "warm_start")

@@ -79,7 +79,7 @@ def test_step_parity_small_and_ragged(solver, m, n, k):
     _step_parity(solver, pr, k, seed=m + n + k)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("tile_k", [1, 2, 4])
 @pytest.mark.parametrize("grid", [37, 0])
 def test_step_parity_every_variant_and_tile_width(variant, tile_k, grid):
@@ -89,19 +89,19 @@ def test_step_parity_every_variant_and_tile_width(variant, tile_k, grid):
         assert s.profile()["step_variant"] == variant and s.profile()["tile_k"] == tile_k
 
 
-@pytest.mark.parametrize("variant", [1, 2])
-def test_variants_agree_bitwise_on_a_solve(variant):
+def test_variants_agree_bitwise_on_a_solve():
     # the two fused-step variants perform the same FP32 operations in the same order
     # per entry and write the same partials, so whole runs agree bit for bit
     pr = workloads.make_problem("plain_8192x6144", seed=12, m=517, n=1029)
     outs = {}
-    for v in (1, 2):
+    for v in (1, 2, 3):
         C, p, q, X, mu, nu = _gpu_inputs(pr)
         with drot.Solver(device=0, step_variant=v, tile_k=2, grid_ctas=53, deterministic=True) as s:
             o = s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=300, X=X, mu=mu, nu=nu)
         outs[v] = (X.cpu().numpy(), mu.cpu().numpy(), o["primal_obj"])
-    assert np.array_equal(outs[1][0], outs[2][0])
-    assert np.array_equal(outs[1][1], outs[2][1]) and outs[1][2] == outs[2][2]
+    for v in (2, 3):
+        assert np.array_equal(outs[1][0], outs[v][0])
+        assert np.array_equal(outs[1][1], outs[v][1]) and outs[1][2] == outs[v][2]
 
 
 def test_step_parity_full_size_8192x6144(solver):
@@ -209,7 +209,7 @@ def test_autotune_picks_a_plan_and_keeps_parity(m, n):
     with drot.Solver(device=0, autotune=True) as s:
         _step_parity(s, pr, 2, seed=5)
         prof = s.profile()
-        assert prof["step_variant"] in (1, 2) and prof["tile_k"] in (1, 2, 4)
+        assert prof["step_variant"] in (1, 2, 3) and prof["tile_k"] in (1, 2, 4)
         first = (prof["step_variant"], prof["tile_k"])
         _step_parity(s, pr, 1, seed=6)  # the choice is cached per shape
         prof = s.profile()
@@ -225,7 +225,7 @@ def test_max_iter_zero_returns_cold_start(solver):
     assert np.array_equal(X.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_deterministic_mode_bitwise(variant):
     pr = workloads.make_problem("plain_8192x6144", seed=3, m=700, n=900)
     outs = []
@@ -257,7 +257,7 @@ def test_host_buffers_match_device_buffers():
     solver.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_accumulation_and_fixed_order_modes_agree(variant):
     # the two summation modes differ only in the order of FP64 additions
     pr = workloads.make_problem("plain_8192x6144", seed=13, m=300, n=1100)

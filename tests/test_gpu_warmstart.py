@@ -1,0 +1,151 @@
+"""Learned warm start: the network's kernels against the FP64 reference, the seed's dual
+feasibility, and the gain of a trained network over cold-start DROT.
+
+Tolerances: the GPU multiplies BF16 operands (8 significant bits) and accumulates in FP32, and
+stores activations in BF16, so each layer carries a relative error of a few 2^-8; forward
+outputs are compared at 5e-2 of their scale and gradients by direction (cosine) and norm.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import mlp as ref_mlp
+from paper_2110_11738_b300 import drot, warmstart
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_features(rows, seed):
+    rng = np.random.default_rng(seed)
+    F = rng.uniform(-1, 1, size=(rows, 64)).astype(np.float32)
+    Fb = torch.as_tensor(F, device="cuda").to(torch.bfloat16)
+    return Fb, Fb.float().cpu().numpy().astype(np.float64)
+
+
+def test_forward_matches_reference():
+    params = workloads.mlp_init_params(3)
+    net = drot.Mlp(0, params)
+    Fb, F64 = _bf16_features(192, 1)
+    out = torch.zeros(192, dtype=torch.float32, device="cuda")
+    net.forward(Fb, out)
+    ref, _ = ref_mlp.forward(params.astype(np.float64), F64)
+    got = out.cpu().numpy()
+    assert np.abs(got - ref).max() <= 5e-2 * np.abs(ref).max()
+    assert np.corrcoef(got, ref)[0, 1] > 0.999
+    net.close()
+
+
+def test_gradients_match_reference():
+    params = workloads.mlp_init_params(4)
+    params[-257:-1] *= 8.0  # larger output weights: gradients well above rounding noise
+    net = drot.Mlp(0, params)
+    rows = 256
+    Fb, F64 = _bf16_features(rows, 2)
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(rows).astype(np.float32)
+    w = rng.uniform(0.1, 1.0, rows).astype(np.float32)
+    seg = rng.integers(0, 4, rows).astype(np.int32)
+    seg[-10:] = -1  # padding rows
+    loss, grad = net.train_step(Fb, torch.as_tensor(y, device="cuda"), torch.as_tensor(w, device="cuda"),
+                                torch.as_tensor(seg, device="cuda"), 4, 0.0, update=False, want_grad=True)
+    keep = seg >= 0
+    L, g = ref_mlp.loss_and_grad(params.astype(np.float64), F64[keep], y[keep].astype(np.float64),
+                                 w[keep].astype(np.float64), seg[keep], 4)
+    assert abs(loss - L) <= 5e-2 * L
+    off = 0
+    for name, shape in ref_mlp.SHAPES:
+        k = int(np.prod(shape))
+        a, b = grad[off:off + k].astype(np.float64), g[off:off + k]
+        off += k
+        nb = np.linalg.norm(b)
+        if nb < 1e-9:
+            continue
+        cos = a @ b / (np.linalg.norm(a) * nb)
+        assert cos > 0.99, (name, cos)
+        assert abs(np.linalg.norm(a) - nb) <= 5e-2 * nb, name
+    # the update actually moves the parameters (Adam step)
+    net.train_step(Fb, torch.as_tensor(y, device="cuda"), torch.as_tensor(w, device="cuda"),
+                   torch.as_tensor(seg, device="cuda"), 4, 1e-3, update=True)
+    assert np.abs(net.get_params() - params).max() > 1e-4
+    net.close()
+
+
+def test_features_match_reference():
+    pr = workloads.make_problem("warm_1024", seed=5, m=300, n=250)
+    net = drot.Mlp(0)
+    feat = torch.zeros((320, 64), dtype=torch.bfloat16, device="cuda")
+    xs = torch.as_tensor(pr.x, dtype=torch.float32, device="cuda").contiguous()
+    yt = torch.as_tensor(pr.y, dtype=torch.float32, device="cuda").contiguous()
+    net.features(xs, yt, torch.as_tensor(pr.p, device="cuda"), torch.as_tensor(pr.q, device="cuda"), feat, 10)
+    got = feat.float().cpu().numpy()
+    ref = ref_mlp.features(pr.x.astype(np.float32).astype(np.float64), pr.y.astype(np.float32).astype(np.float64),
+                           pr.p, pr.q)
+    assert np.abs(got[10:310] - ref).max() <= 1e-2 * max(1.0, np.abs(ref).max())
+    assert np.all(got[:10] == 0) and np.all(got[310:] == 0)
+    net.close()
+
+
+def test_seed_is_dual_feasible_and_tight():
+    pr = workloads.make_problem("warm_1024", seed=6, m=200, n=170)
+    net = drot.Mlp(0, workloads.mlp_init_params(7))
+    d = warmstart._device_problem(pr, 0)
+    xs = torch.as_tensor(pr.x, dtype=torch.float32, device="cuda").contiguous()
+    yt = torch.as_tensor(pr.y, dtype=torch.float32, device="cuda").contiguous()
+    net.warm_start(xs, yt, d["p"], d["q"], pr.cost_scale, d["C"], d["X"], d["mu"], d["nu"])
+    C = torch.as_tensor(pr.C, dtype=torch.float64, device="cuda")
+    slack = C - d["mu"][:, None] - d["nu"][None, :]
+    assert float(slack.min()) >= -1e-12
+    assert float(slack.min(dim=1).values.abs().max()) <= 1e-12  # every row tight
+    assert float(slack.min(dim=0).values.abs().max()) <= 1e-12  # every column tight
+    assert np.array_equal(d["X"].cpu().numpy(), np.outer(pr.p, pr.q).astype(np.float32))
+    net.close()
+
+
+def _weighted_corr(a, b, w):
+    a = a - (w * a).sum()
+    b = b - (w * b).sum()
+    return (w * a * b).sum() / np.sqrt((w * a * a).sum() * (w * b * b).sum())
+
+
+def test_trained_network_predicts_duals_and_seeds_faster_solves():
+    """Train on DROT's own solutions of small mixture-of-Gaussians problems, then, on held-out
+    problems of the same family: the trained network's potentials correlate with the solved
+    duals far better than the untrained one's, warm-started solves reach the cold-start
+    objective, and under the paper's full primal-dual stopping test (gap, l1 residual and
+    dual residual) they need fewer iterations on average than cold starts."""
+    m = 128
+    rule = drot.STOP_GAP | drot.STOP_RES_L1 | drot.STOP_DUAL_RES
+    train_probs = [workloads.make_problem("warm_1024", seed=1000 + s, m=m, n=m) for s in range(128)]
+    held_out = [workloads.make_problem("warm_1024", seed=5000 + s, m=m, n=m) for s in range(8)]
+    with drot.Solver(device=0, stop_rule=rule) as solver:
+        mus, res = warmstart.solve_labels(train_probs, solver, tol=1e-5, max_iter=2_000_000)
+        assert all(r["status"] == drot.DROT_OK for r in res)
+        untrained = drot.Mlp(0, workloads.mlp_init_params(11))
+        net = drot.Mlp(0, workloads.mlp_init_params(11))
+        ts = warmstart.build_training_set(train_probs, mus, net)
+        losses = warmstart.train(net, ts, steps=600, batch=16, lr=2e-3, seed=1)
+        assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:20])
+        cold, warm, corr_t, corr_u = [], [], [], []
+        for pr in held_out:
+            c = warmstart.cold_solve(solver, pr, tol=1e-5, max_iter=3_000_000)
+            assert c["status"] == drot.DROT_OK
+            mu_star = c["mu"].cpu().numpy()
+            for model, sink in ((net, corr_t), (untrained, corr_u)):
+                d = warmstart._device_problem(pr, 0)
+                xs = torch.as_tensor(pr.x, dtype=torch.float32, device="cuda").contiguous()
+                yt = torch.as_tensor(pr.y, dtype=torch.float32, device="cuda").contiguous()
+                model.warm_start(xs, yt, d["p"], d["q"], pr.cost_scale, d["C"], d["X"], d["mu"], d["nu"])
+                sink.append(_weighted_corr(d["mu"].cpu().numpy(), mu_star, pr.p))
+            w = warmstart.warm_solve(net, solver, pr, tol=1e-5, max_iter=3_000_000)
+            assert w["status"] == drot.DROT_OK
+            assert abs(w["primal_obj"] - c["primal_obj"]) <= 1e-4 * c["primal_obj"] + 1e-5
+            cold.append(c["iters"])
+            warm.append(w["iters"])
+        net.close()
+        untrained.close()
+    print(f"warm-start: duals corr trained {np.mean(corr_t):.4f} vs untrained {np.mean(corr_u):.4f}; "
+          f"iterations cold {np.mean(cold):.0f} warm {np.mean(warm):.0f} ({cold} / {warm})")
+    assert np.mean(corr_t) > 0.9 and np.mean(corr_t) > np.mean(corr_u) + 0.05
+    assert np.mean(warm) < np.mean(cold), (cold, warm)

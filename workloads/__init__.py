@@ -12,6 +12,7 @@ from .synthetic import (  # noqa: F401
     make_problem,
     make_batch,
     random_start,
+    mlp_init_params,
     sq_euclidean_cost_np,
     sq_euclidean_cost_torch,
     default_rho,

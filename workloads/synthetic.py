@@ -51,6 +51,7 @@ class Problem:
     tol: float
     x: Optional[np.ndarray] = None  # source points (m, dim), float64
     y: Optional[np.ndarray] = None  # target points (n, dim), float64
+    cost_scale: float = 1.0         # C = squared distances / cost_scale
 
 
 def default_rho(m: int, n: int, rho0: float = 2.0) -> float:
@@ -67,8 +68,11 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
 
 
-def sq_euclidean_cost_np(x: np.ndarray, y: np.ndarray, block_rows: int = 4096) -> np.ndarray:
-    """FP32 matrix of ||x_i - y_j||^2 / max_ij ||x_i - y_j||^2 (built in FP64)."""
+def sq_euclidean_cost_np(x: np.ndarray, y: np.ndarray, block_rows: int = 4096, return_scale: bool = False):
+    """FP32 matrix of ||x_i - y_j||^2 / max_ij ||x_i - y_j||^2 (built in FP64).
+
+    With ``return_scale`` also returns the divisor max_ij ||x_i - y_j||^2.
+    """
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     m, d = x.shape
@@ -92,11 +96,11 @@ def sq_euclidean_cost_np(x: np.ndarray, y: np.ndarray, block_rows: int = 4096) -
         b = block(i0, i1)
         b /= cmax
         out[i0:i1] = b.astype(np.float32)
-    return out
+    return (out, cmax) if return_scale else out
 
 
 def sq_euclidean_cost_torch(x: np.ndarray, y: np.ndarray, device="cpu", ld: Optional[int] = None,
-                            block_rows: int = 2048):
+                            block_rows: int = 2048, return_scale: bool = False):
     """Same matrix as :func:`sq_euclidean_cost_np`, built with torch on ``device``.
 
     Returns a float32 tensor of shape (m, ld) whose first n columns hold the
@@ -129,7 +133,7 @@ def sq_euclidean_cost_torch(x: np.ndarray, y: np.ndarray, device="cpu", ld: Opti
         b = block(i0, i1)
         b /= cmax_v
         out[i0:i1, :n] = b.to(torch.float32)
-    return out
+    return (out, cmax_v) if return_scale else out
 
 
 def _marginal(rng: np.random.Generator, k: int, kind: str) -> np.ndarray:
@@ -202,11 +206,11 @@ def make_problem(name: str, seed: int = 0, m: Optional[int] = None, n: Optional[
     q = _marginal(rng, n, spec["marginals"])
     p, q = _rescale_mass(p, q)
     if device is None:
-        C = sq_euclidean_cost_np(x, y)
+        C, scale = sq_euclidean_cost_np(x, y, return_scale=True)
     else:
-        C = sq_euclidean_cost_torch(x, y, device=device, ld=ld)
+        C, scale = sq_euclidean_cost_torch(x, y, device=device, ld=ld, return_scale=True)
     return Problem(name=name, seed=seed, m=m, n=n, C=C, p=p, q=q,
-                   rho=default_rho(m, n, spec["rho0"]), tol=float(spec["tol"]), x=x, y=y)
+                   rho=default_rho(m, n, spec["rho0"]), tol=float(spec["tol"]), x=x, y=y, cost_scale=float(scale))
 
 
 def make_batch(name: str = "batched_512", seed: int = 0, B: Optional[int] = None,
@@ -227,10 +231,26 @@ def make_batch(name: str = "batched_512", seed: int = 0, B: Optional[int] = None
         p = _marginal(r, m, spec["marginals"])
         q = _marginal(r, n, spec["marginals"])
         p, q = _rescale_mass(p, q)
-        probs.append(Problem(name=f"{name}[{b}]", seed=int(seeds[b]), m=m, n=n,
-                             C=sq_euclidean_cost_np(x, y), p=p, q=q,
-                             rho=default_rho(m, n, spec["rho0"]), tol=float(spec["tol"]), x=x, y=y))
+        C, scale = sq_euclidean_cost_np(x, y, return_scale=True)
+        probs.append(Problem(name=f"{name}[{b}]", seed=int(seeds[b]), m=m, n=n, C=C, p=p, q=q,
+                             rho=default_rho(m, n, spec["rho0"]), tol=float(spec["tol"]), x=x, y=y,
+                             cost_scale=float(scale)))
     return probs
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Initial parameters of the warm-start network (flat FP32, layout of drot_mlp_set_params).
+
+    He-normal weights (std sqrt(2 / fan_in)) for the three hidden layers, std 1/16 for the
+    output weights, zero biases.
+    """
+    rng = _rng(seed)
+    fin, width = 64, 256
+    parts = [rng.standard_normal(width * fin) * np.sqrt(2.0 / fin), np.zeros(width),
+             rng.standard_normal(width * width) * np.sqrt(2.0 / width), np.zeros(width),
+             rng.standard_normal(width * width) * np.sqrt(2.0 / width), np.zeros(width),
+             rng.standard_normal(width) / 16.0, np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
 
 
 def random_start(m: int, n: int, seed: int):
