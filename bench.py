@@ -223,7 +223,8 @@ def run_ours(args):
 
     rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
     solver = drot.Solver(device=local, profile=True, stop_rule=rule, step_variant=args.step_variant,
-                         autotune=not args.no_autotune, deterministic=args.deterministic)
+                         autotune=not args.no_autotune and not args.persistent,
+                         deterministic=args.deterministic, persistent=args.persistent)
 
     def one_solve():
         return solver.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
@@ -321,7 +322,8 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 (C+X = {2 * m * ld * 4 / 1e6:.0f} MB > 126 MB)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "sums": "fixed-order partials" if args.deterministic else "FP64 atomics",
-                   "plan": "autotuned" if not args.no_autotune else "default"},
+                   "plan": "autotuned" if not args.no_autotune and not args.persistent else "default",
+                   "iteration": "persistent cooperative launch" if args.persistent else "CUDA graphs"},
         "iters_to_tol": iters,
         "status": statuses,
         "ms_per_iter": ms_per_solve / statistics.mean(iters),
@@ -359,6 +361,7 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--stop", choices=["gap", "full"], default="gap")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default plan")
+    ap.add_argument("--persistent", action="store_true", help="one cooperative launch runs the iterations")
     ap.add_argument("--deterministic", action="store_true", help="fixed-order partial sums instead of atomics")
     ap.add_argument("--step-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="fused step: 1 register-fed, 2 TMA-fed, 3 async-copy-fed, 0 library default")

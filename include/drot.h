@@ -94,6 +94,9 @@ typedef struct {
     int autotune;               /* 1: on the first solve of each (m, n), time the fused-step variants and tile
                                    widths on a scratch plan and keep the fastest (costs one m x ld FP32
                                    scratch buffer and a few launches); explicit step_variant / tile_k win */
+    int persistent;             /* 1: run the iterations in one cooperative launch (every CTA resident, two
+                                   bounded grid barriers per iteration, register-fed step, FP64-atomic
+                                   totals); 0: CUDA graphs of [step, finish] launches (default) */
 } drot_config;
 
 typedef struct {

@@ -106,6 +106,23 @@ int async_occupancy() {
 }
 
 template <int K>
+int persistent_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, drot::drot_persistent_kernel<K>, drot::kThreads, 0) !=
+        cudaSuccess)
+        return -1;
+    return nb;
+}
+
+template <int K>
+cudaError_t launch_persistent(int G, drot::StepArgs A, drot::FinishArgs F, drot::GridSync *gs, long long budget,
+                              cudaStream_t s) {
+    void *args[] = {&A, &F, &gs, &budget};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(drot::drot_persistent_kernel<K>), dim3(G),
+                                       dim3(drot::kThreads), args, 0, s);
+}
+
+template <int K>
 int ldg_occupancy() {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, drot::drot_step_kernel<K, true>, drot::kThreads, 0) !=
@@ -150,6 +167,7 @@ struct drot_handle {
     double *g = nullptr, *h = nullptr, *a = nullptr, *b = nullptr;
     double *rowpart = nullptr, *colpart = nullptr, *ctapart = nullptr, *finpart = nullptr;
     double *u = nullptr, *v = nullptr, *acc = nullptr;
+    drot::GridSync *gsync = nullptr;
     long long *wbound = nullptr;
     int *slot_base = nullptr, *tile_slot = nullptr;
 
@@ -157,6 +175,7 @@ struct drot_handle {
     std::string last_error;
 
     int occ[4][5] = {};  // resident CTAs per SM of the fused step [variant][K]
+    int occ_persistent[5] = {};  // resident CTAs per SM of the persistent solve kernel [K]
     struct Tuned {
         long long m, n;
         int variant, K;
@@ -183,6 +202,11 @@ cudaError_t fill_occupancy(drot_handle *h) {
             if (v[a][k] < 0) return cudaErrorUnknown;
             h->occ[a][k] = v[a][k];
         }
+    const int pk[3] = {persistent_occupancy<1>(), persistent_occupancy<2>(), persistent_occupancy<4>()};
+    if (pk[0] < 0 || pk[1] < 0 || pk[2] < 0) return cudaErrorUnknown;
+    h->occ_persistent[1] = pk[0];
+    h->occ_persistent[2] = pk[1];
+    h->occ_persistent[4] = pk[2];
     return cudaSuccess;
 }
 
@@ -261,15 +285,22 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
     P.variant = variant;
     P.S = variant == 2 ? tma_stages(K) : (variant == 3 ? async_stages(K) : 0);
     P.accumulate = h->cfg.deterministic ? 0 : 1;
+    if (h->cfg.persistent) {
+        P.variant = variant = 1;
+        P.S = 0;
+        P.accumulate = 1;
+    }
     int G = h->cfg.grid_ctas;
     if (G <= 0) {
         // as many CTAs as fit on the SMs at once (one wave); small problems use fewer
         // CTAs so that each warp has rows
         const long long want = (units + drot::kWarps - 1) / drot::kWarps;
-        const long long per_sm = std::max(1, h->occ[variant][K]);
+        const long long per_sm = std::max(1, h->cfg.persistent ? h->occ_persistent[K] : h->occ[variant][K]);
         G = (int)std::min<long long>(per_sm * h->num_sms, std::max<long long>(1, want));
     }
     G = (int)std::min<long long>(G, std::max<long long>(1, units));
+    // a cooperative launch needs every CTA resident at once
+    if (h->cfg.persistent) G = std::min(G, std::max(1, h->occ_persistent[K]) * h->num_sms);
     P.G = G;
 
     const long long last_w = n - (long long)(P.T - 1) * P.TW;  // columns of the last tile
@@ -305,6 +336,7 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
     const long long mn = m + n;
     P.fin_blocks = (int)std::min<long long>(2LL * h->num_sms,
                                             std::max<long long>(1, (mn + drot::kFinishThreads - 1) / drot::kFinishThreads));
+    if (h->cfg.persistent) P.fin_blocks = G;  // the finish phase runs on the same CTAs
 
     int gi = h->cfg.graph_iters;
     if (gi <= 0) {
@@ -330,7 +362,7 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
                          align_up(sizeof(double) * drot::kFinishAcc * P.fin_blocks, 256) +
                          align_up(sizeof(long long) * (P.G + 1), 256) + align_up(sizeof(int) * P.G, 256) +
                          align_up(sizeof(int) * (P.T + 1), 256) + align_up(sizeof(double) * m, 256) +
-                         align_up(sizeof(double) * n, 256) + 256 + 4096;
+                         align_up(sizeof(double) * n, 256) + 256 + align_up(sizeof(drot::GridSync), 256) + 4096;
     drot_status st = arena_reserve(h, h->work, bytes);
     if (st != DROT_OK) return st;
     char *cur = static_cast<char *>(h->work.ptr);
@@ -349,6 +381,8 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
     h->u = carve<double>(cur, m);
     h->v = carve<double>(cur, n);
     h->acc = carve<double>(cur, 2);
+    h->gsync = carve<drot::GridSync>(cur, 1);
+    DROT_CUDA(h, cudaMemsetAsync(h->gsync, 0, sizeof(drot::GridSync), h->stream));
     if (P.accumulate) {
         // totals start at zero; every finish pass resets what it reads
         DROT_CUDA(h, cudaMemsetAsync(h->u, 0, sizeof(double) * m, h->stream));
@@ -599,7 +633,34 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
 
     long long iters_done = 0;
     int done = max_iter > 0 ? drot::kRunning : drot::kIterCap;
-    if (max_iter > 0) {
+    if (max_iter > 0 && h->cfg.persistent) {
+        // one cooperative launch runs up to `budget` iterations (about half a second of work)
+        const double t_iter = 12.0 * (double)m * (double)n / 6.0e12 + 8.0e-6;
+        const long long budget = std::max(1LL, std::min<long long>(max_iter, std::llround(0.5 / t_iter)));
+        const long long max_launches = (max_iter + budget - 1) / budget + 2;
+        for (long long l = 0; l < max_launches; ++l) {
+            cudaError_t e = cudaSuccess;
+            switch (P.K) {
+                case 1: e = launch_persistent<1>(P.G, A, F, h->gsync, budget, h->stream); break;
+                case 2: e = launch_persistent<2>(P.G, A, F, h->gsync, budget, h->stream); break;
+                default: e = launch_persistent<4>(P.G, A, F, h->gsync, budget, h->stream); break;
+            }
+            if (e != cudaSuccess) return fail(h, DROT_ERR_CUDA, "cooperative launch failed: %s", cudaGetErrorString(e));
+            h->prof.kernel_launches += 1;
+            DROT_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (h->h_status->done != drot::kRunning || h->h_status->fault) {
+                done = h->h_status->fault ? drot::kFault : h->h_status->done;
+                break;
+            }
+        }
+        drot::GridSync gs{};
+        DROT_CUDA(h, cudaMemcpy(&gs, h->gsync, sizeof gs, cudaMemcpyDeviceToHost));
+        h->prof.step_ms_total += (double)gs.step_ns * 1e-6;
+        h->prof.step_launches += (long long)gs.iters;
+        if (done == drot::kRunning)
+            return fail(h, DROT_ERR_CUDA, "persistent iteration did not report completion");
+    } else if (max_iter > 0) {
         GraphKey key;
         key.m = m; key.n = n; key.ld = ld; key.C = C; key.X = X; key.p = p; key.q = q;
         key.arena = h->work.ptr; key.K = P.K; key.G = P.G; key.graph_iters = P.graph_iters;
@@ -1068,6 +1129,7 @@ void drot_config_default(drot_config *cfg) {
     cfg->step_variant = 0;
     cfg->deterministic = 0;
     cfg->autotune = 0;
+    cfg->persistent = 0;
 }
 
 drot_status drot_create(drot_handle **out, const drot_config *cfg) {

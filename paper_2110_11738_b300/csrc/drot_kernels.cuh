@@ -136,21 +136,19 @@ __device__ __forceinline__ float4 ld_stream_ro(const float* p) {
 // The fused DR pass (UPDATE = true) or a plain row/column-sum pass over X
 // (UPDATE = false, used once to initialise a_0 and b_0 from the stored X_0).
 template <int K, bool UPDATE>
-__global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
+__device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
     constexpr int TW = 128 * K;
     __shared__ double s_col[kWarps][TW];
     __shared__ double s_red[kWarps][2];
 
-    if (A.sc->done != kRunning) return;
-
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const long long m = A.m, n = A.n, ld = A.ld;
-    const long long w0 = A.wbound[blockIdx.x];
-    const long long w1 = A.wbound[blockIdx.x + 1];
+    const long long w0 = A.wbound[cta];
+    const long long w1 = A.wbound[cta + 1];
     const float rho = UPDATE ? (float)A.sc->rho : 0.f;
-    const double cs = A.sc->c;
-    int slot = A.slot_base[blockIdx.x];
+    const double cs = __ldcg(&A.sc->c);
+    int slot = A.slot_base[cta];
     double scx64 = 0.0, sd64 = 0.0;
 
     long long w = w0;
@@ -166,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const long long j = col0 + kk * 128 + lane * 4 + e;
-                psi[kk][e] = (UPDATE && j < n) ? (float)((A.h[j] + cs) * A.inv_m) : 0.f;
+                psi[kk][e] = (UPDATE && j < n) ? (float)((__ldcg(A.h + j) + cs) * A.inv_m) : 0.f;
                 cacc[kk][e] = 0.f;
             }
         }
@@ -176,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
         float scx = 0.f, sd = 0.f;
         int since_flush = 0;
         for (long long i = i0 + warp; i < i1; i += kWarps) {
-            const float phi = UPDATE ? (float)((A.g[i] + cs) * A.inv_n) : 0.f;
+            const float phi = UPDATE ? (float)((__ldcg(A.g + i) + cs) * A.inv_n) : 0.f;
             const long long rowoff = i * ld + col0 + lane * 4;
             float4 xv[K], cv[K];
 #pragma unroll
@@ -270,11 +268,17 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
                 atomicAdd(A.acc + 0, v[0]);
                 atomicAdd(A.acc + 1, v[1]);
             } else {
-                A.ctapart[2 * blockIdx.x + 0] = v[0];
-                A.ctapart[2 * blockIdx.x + 1] = v[1];
+                A.ctapart[2 * cta + 0] = v[0];
+                A.ctapart[2 * cta + 1] = v[1];
             }
         }
     }
+}
+
+template <int K, bool UPDATE>
+__global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
+    if (A.sc->done != kRunning) return;
+    step_body<K, UPDATE>(A, blockIdx.x);
 }
 
 
@@ -786,12 +790,12 @@ __device__ __forceinline__ double strided_total(const double* base, long long st
     for (; t + 8 <= count; t += 8) {
         double v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = base[(long long)(t + u) * stride];
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(base + (long long)(t + u) * stride);
         a0 += v[0]; a1 += v[1]; a2 += v[2]; a3 += v[3];
         a0 += v[4]; a1 += v[5]; a2 += v[6]; a3 += v[7];
     }
     for (; t < count; ++t) {
-        const double v = base[(long long)t * stride];
+        const double v = __ldcg(base + (long long)t * stride);
         switch (t & 3) {
             case 0: a0 += v; break;
             case 1: a1 += v; break;
@@ -804,7 +808,7 @@ __device__ __forceinline__ double strided_total(const double* base, long long st
 
 __device__ __forceinline__ double row_total(const FinishArgs& A, long long i) {
     if (A.accumulate) {
-        const double u = A.u[i];
+        const double u = __ldcg(A.u + i);
         A.u[i] = 0.0;
         return u;
     }
@@ -813,7 +817,7 @@ __device__ __forceinline__ double row_total(const FinishArgs& A, long long i) {
 
 __device__ __forceinline__ double col_total(const FinishArgs& A, long long j) {
     if (A.accumulate) {
-        const double v = A.v[j];
+        const double v = __ldcg(A.v + j);
         A.v[j] = 0.0;
         return v;
     }
@@ -839,21 +843,22 @@ __device__ __forceinline__ bool arrive_last(Scalars* sc, int nblk) {
 }
 
 // Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1), executed by block
-// `blk` of the `nblk` blocks that serve this problem.
+// `blk` of the `nblk` blocks (of NT threads) that serve this problem.
+template <int NT = kFinishThreads>
 __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nblk) {
-    __shared__ double s_red[kFinishThreads / 32][kFinishAcc];
+    __shared__ double s_red[NT / 32][kFinishAcc];
     Scalars* sc = A.sc;
 
     // acc: 0 sum r, 1 ||r||_1 + ||s||_1, 2 ||r||^2 + ||s||^2, 3 p.g', 4 q.h', 5 sum s
     double acc[kFinishAcc] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const long long mn = A.m + A.n;
-    for (long long idx = (long long)blk * kFinishThreads + threadIdx.x; idx < mn;
-         idx += (long long)nblk * kFinishThreads) {
+    for (long long idx = (long long)blk * NT + threadIdx.x; idx < mn; idx += (long long)nblk * NT) {
         if (idx < A.m) {
             const long long i = idx;
             const double r = row_total(A, i) - A.p[i];
-            const double gn = A.a[i] - 2.0 * r;
-            A.a[i] -= r;
+            const double ai = __ldcg(A.a + i);
+            const double gn = ai - 2.0 * r;
+            A.a[i] = ai - r;
             A.g[i] = gn;
             acc[0] += r;
             acc[1] += fabs(r);
@@ -862,8 +867,9 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
         } else {
             const long long j = idx - A.m;
             const double s = col_total(A, j) - A.q[j];
-            const double hn = A.b[j] - 2.0 * s;
-            A.b[j] -= s;
+            const double bj = __ldcg(A.b + j);
+            const double hn = bj - 2.0 * s;
+            A.b[j] = bj - s;
             A.h[j] = hn;
             acc[5] += s;
             acc[1] += fabs(s);
@@ -871,7 +877,7 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
             acc[4] += A.q[j] * hn;
         }
     }
-    block_sum_f64<kFinishAcc, kFinishThreads>(acc, s_red);
+    block_sum_f64<kFinishAcc, NT>(acc, s_red);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int c = 0; c < kFinishAcc; ++c) A.finpart[blk * kFinishAcc + c] = acc[c];
@@ -882,7 +888,7 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
     // CTAs of the step launch.
     double tot[kFinishAcc + 2];
     for (int c = 0; c < kFinishAcc + 2; ++c) tot[c] = 0.0;
-    for (int bidx = threadIdx.x; bidx < nblk; bidx += kFinishThreads)
+    for (int bidx = threadIdx.x; bidx < nblk; bidx += NT)
         for (int c = 0; c < kFinishAcc; ++c) tot[c] += __ldcg(A.finpart + bidx * kFinishAcc + c);
     if (A.accumulate) {
         if (threadIdx.x == 0) {
@@ -892,16 +898,17 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
             A.acc[1] = 0.0;
         }
     } else {
-        for (int bidx = threadIdx.x; bidx < A.G; bidx += kFinishThreads) {
+        for (int bidx = threadIdx.x; bidx < A.G; bidx += NT) {
             tot[kFinishAcc + 0] += __ldcg(A.ctapart + 2 * bidx + 0);
             tot[kFinishAcc + 1] += __ldcg(A.ctapart + 2 * bidx + 1);
         }
     }
-    __shared__ double s_red2[kFinishThreads / 32][kFinishAcc + 2];
-    block_sum_f64<kFinishAcc + 2, kFinishThreads>(tot, s_red2);
+    __shared__ double s_red2[NT / 32][kFinishAcc + 2];
+    block_sum_f64<kFinishAcc + 2, NT>(tot, s_red2);
     if (threadIdx.x == 0) {
+        const double alpha = __ldcg(&sc->alpha);
         const double beta = tot[0] * A.inv_mn;            // step 5
-        const double c_new = 2.0 * beta - sc->alpha;       // steps 6-7 scalar term
+        const double c_new = 2.0 * beta - alpha;           // steps 6-7 scalar term
         const double pphi = (tot[3] + c_new * sc->sum_p) * A.inv_n;
         const double qpsi = (tot[4] + c_new * sc->sum_q) * A.inv_m;
         const double inv_rho = sc->inv_rho;
@@ -911,7 +918,7 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
         const double res_l1 = tot[1];
         const double res_l2 = sqrt(tot[2]);
         const double dres = sqrt(tot[kFinishAcc + 1]) * inv_rho;
-        sc->alpha -= beta;                                 // step 8
+        sc->alpha = alpha - beta;                          // step 8
         sc->c = c_new;
         sc->beta = beta;
         sc->primal = primal;
@@ -920,7 +927,7 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
         sc->res_l1 = res_l1;
         sc->res_l2 = res_l2;
         sc->dual_res_prev = dres;
-        const long long k = sc->k + 1;
+        const long long k = __ldcg(&sc->k) + 1;
         sc->k = k;
         const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2) &&
                             isfinite(dres) && isfinite(c_new) && isfinite(tot[5]);
@@ -928,7 +935,7 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
         const bool conv = (!(rule & 1) || gap <= sc->tol) && (!(rule & 2) || res_l1 <= sc->tol) &&
                           (!(rule & 4) || dres <= sc->tol);
         int done = kRunning;
-        if (sc->fault) done = kFault;
+        if (__ldcg(&sc->fault)) done = kFault;
         else if (!finite) done = kNonFinite;
         else if (conv) done = kConverged;
         else if (k >= sc->max_iter) done = kIterCap;
@@ -940,7 +947,82 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
 
 __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs A) {
     if (A.sc->done != kRunning) return;
-    finish_body(A, blockIdx.x, gridDim.x);
+    finish_body<kFinishThreads>(A, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------------------------ persistent solve
+//
+// One cooperative launch (every CTA resident) runs up to `budget` iterations:
+// fused step -> grid barrier -> finish (elements spread over all CTAs, scalar part
+// in the last CTA to arrive) -> grid barrier.  The grid barrier is a counter and a
+// generation word; a CTA that waits longer than kBarrierSpins polls records a
+// fault in Scalars and leaves, and every other CTA then leaves at its next wait,
+// so a broken launch ends instead of hanging.
+
+constexpr unsigned long long kBarrierSpins = 1ull << 24;
+
+struct GridSync {
+    unsigned int count;
+    unsigned int gen;
+    unsigned long long step_ns;  // time from each step's start to the end of its barrier (CTA 0)
+    unsigned long long iters;    // iterations timed
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false (in every thread of the CTA) if the barrier gave up.
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, Scalars* sc) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = &gs->gen;
+        volatile int* fault = &sc->fault;
+        const unsigned int my_gen = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&gs->count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == my_gen) {
+                if (++spins > kBarrierSpins || ((spins & 255ull) == 0 && *fault)) {
+                    atomicExch(&sc->fault, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, 2) drot_persistent_kernel(StepArgs A, FinishArgs F, GridSync* gs,
+                                                                      long long budget) {
+    Scalars* sc = F.sc;
+    for (long long it = 0; it < budget; ++it) {
+        if (*(volatile int*)&sc->done != kRunning) break;  // uniform: read after a barrier
+        const unsigned long long t0 = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
+        step_body<K, true>(A, blockIdx.x);
+        if (!grid_barrier(gs, sc)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            gs->step_ns += global_ns() - t0;
+            gs->iters += 1;
+        }
+        finish_body<kThreads>(F, blockIdx.x, gridDim.x);
+        if (!grid_barrier(gs, sc)) return;
+    }
 }
 
 // ---------------------------------------------------------------- set-up / tear-down

@@ -216,6 +216,34 @@ def test_autotune_picks_a_plan_and_keeps_parity(m, n):
         assert (prof["step_variant"], prof["tile_k"]) == first
 
 
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 7), (33, 129), (257, 1031), (300, 2053), (1000, 64)])
+def test_persistent_step_parity(m, n):
+    pr = workloads.make_problem("plain_8192x6144", seed=m * 7 + n, m=m, n=n)
+    with drot.Solver(device=0, persistent=True) as s:
+        _step_parity(s, pr, 3, seed=m + 2 * n)
+        assert s.profile()["kernel_launches"] >= 1
+
+
+def test_persistent_solve_parity_plain_256():
+    pr = workloads.make_problem("plain_256", seed=0)
+    with drot.Solver(device=0, persistent=True) as s:
+        out, ref = _solve_parity(s, pr)
+    assert 0.5 * ref["iters"] <= out["iters"] <= 2.0 * ref["iters"]
+
+
+def test_persistent_matches_graph_iteration():
+    pr = workloads.make_problem("plain_8192x6144", seed=21, m=900, n=700)
+    outs = []
+    for persistent in (False, True):
+        C, p, q, X, mu, nu = _gpu_inputs(pr)
+        with drot.Solver(device=0, persistent=persistent, step_variant=1) as s:
+            o = s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=500, X=X, mu=mu, nu=nu)
+        outs.append((X.cpu().numpy().astype(np.float64), o))
+    assert outs[0][1]["iters"] == outs[1][1]["iters"] == 500
+    assert np.abs(outs[0][0] - outs[1][0]).max() <= 1e-6 * np.abs(outs[0][0]).max()
+    assert abs(outs[0][1]["primal_obj"] - outs[1][1]["primal_obj"]) <= 1e-6 * outs[0][1]["primal_obj"]
+
+
 def test_max_iter_zero_returns_cold_start(solver):
     pr = workloads.make_problem("plain_256", seed=2, m=9, n=13)
     C, p, q, X, mu, nu = _gpu_inputs(pr)
