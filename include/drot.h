@@ -97,6 +97,17 @@ typedef struct {
     int persistent;             /* 1: run the iterations in one cooperative launch (every CTA resident, two
                                    bounded grid barriers per iteration, register-fed step, FP64-atomic
                                    totals); 0: CUDA graphs of [step, finish] launches (default) */
+    int c_skip;                 /* 1: skip the load of C every other iteration (Claim 1, Sec. 3.3): passes
+                                   alternate between reading X and C while storing X - rho C, and reading
+                                   only that array; 10 instead of 12 bytes per entry on average.  The
+                                   stopping test runs after the C-reading passes only.  Uses the
+                                   register-fed step and CUDA graphs (persistent is ignored) */
+    int cluster;                /* small problems on one thread-block cluster (X and C held in shared
+                                   memory for the whole solve, column and scalar totals exchanged in
+                                   distributed shared memory): 0 automatic (used when the problem fits
+                                   and none of step_variant, tile_k, grid_ctas, persistent,
+                                   deterministic, c_skip is set), 1 never, 2 required
+                                   (DROT_ERR_INVALID_ARG if the problem does not fit; c_skip off) */
 } drot_config;
 
 typedef struct {

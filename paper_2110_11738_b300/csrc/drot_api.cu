@@ -23,6 +23,7 @@
 #include "drot_kernels.cuh"
 #include "drot_batched.cuh"
 #include "drot_mlp.cuh"
+#include "drot_cluster.cuh"
 
 using drot::Scalars;
 
@@ -41,11 +42,11 @@ struct GraphKey {
     long long m = -1, n = -1, ld = -1;
     const void *C = nullptr, *X = nullptr, *p = nullptr, *q = nullptr;
     const void *arena = nullptr;
-    int K = 0, G = 0, graph_iters = 0, profile = 0, variant = 0, accumulate = 0;
+    int K = 0, G = 0, graph_iters = 0, profile = 0, variant = 0, accumulate = 0, c_skip = 0;
     bool operator==(const GraphKey &o) const {
         return m == o.m && n == o.n && ld == o.ld && C == o.C && X == o.X && p == o.p && q == o.q &&
                arena == o.arena && K == o.K && G == o.G && graph_iters == o.graph_iters && profile == o.profile &&
-               variant == o.variant && accumulate == o.accumulate;
+               variant == o.variant && accumulate == o.accumulate && c_skip == o.c_skip;
     }
 };
 
@@ -59,6 +60,25 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Ring depth of the TMA-fed step for a tile width (each stage holds 8 rows of X and C).
 // K = 4 rings take 160 KB (one CTA per SM); K = 2 and K = 1 rings fit two CTAs per SM.
 int tma_stages(int K) { return K == 4 ? 4 : (K == 2 ? 4 : 8); }
+
+// Launch `kernel`; with pdl, as a programmatic dependent of the previous kernel in the
+// stream (its launch and set-up overlap that kernel's tail; the kernel itself waits in
+// griddepcontrol.wait before reading anything the previous kernel wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                     Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 template <int K, int S>
 cudaError_t set_tma_attr() {
@@ -75,6 +95,51 @@ cudaError_t set_async_attr() {
 // Ring depth of the async-copy-fed step per tile width (two CTAs per SM).
 int async_stages(int K) { return K == 4 ? 3 : (K == 2 ? 4 : 6); }
 
+// Cluster-resident solve: cluster size and per-CTA shared memory for a problem, or 0
+// if it does not fit on one cluster.
+constexpr size_t kClusterSmemMax = 200 * 1024;
+
+struct ClusterPlan {
+    int cs = 0, R = 0, Q = 0, npad = 0;
+    size_t smem = 0;
+};
+
+ClusterPlan cluster_plan(long long m, long long n) {
+    ClusterPlan cp;
+    for (int cs : {16, 8}) {
+        if (m < cs || n < cs) continue;
+        const int R = (int)((m + cs - 1) / cs), Q = (int)((n + cs - 1) / cs);
+        const int npad = (int)((n + 3) / 4 * 4);
+        const size_t bytes = drot::cluster_smem_bytes(R, Q, npad, n);
+        if (bytes <= kClusterSmemMax) {
+            cp.cs = cs;
+            cp.R = R;
+            cp.Q = Q;
+            cp.npad = npad;
+            cp.smem = bytes;
+            return cp;
+        }
+    }
+    return cp;
+}
+
+template <int CS>
+cudaError_t launch_cluster(const ClusterPlan &cp, const drot::ClusterArgs &args, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(drot::kClusterThreads);
+    cfg.dynamicSmemBytes = cp.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, drot::drot_cluster_kernel<CS>, args);
+}
+
 // Opt the ring-fed kernels into their shared-memory size on the current device
 // (done once per handle, outside any stream capture).
 cudaError_t set_kernel_attributes() {
@@ -84,6 +149,14 @@ cudaError_t set_kernel_attributes() {
     if (e == cudaSuccess) e = set_async_attr<1, 6>();
     if (e == cudaSuccess) e = set_async_attr<2, 4>();
     if (e == cudaSuccess) e = set_async_attr<4, 3>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(drot::drot_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kClusterSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(drot::drot_cluster_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(drot::drot_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kClusterSmemMax);
     return e;
 }
 
@@ -132,15 +205,15 @@ int ldg_occupancy() {
 }
 
 template <int K, int S>
-cudaError_t launch_async(int G, const drot::StepArgs &A, cudaStream_t s) {
-    drot::drot_step_async_kernel<K, S><<<G, drot::kThreads, drot::AsyncLayout<K, S>::bytes, s>>>(A);
-    return cudaGetLastError();
+cudaError_t launch_async(int G, const drot::StepArgs &A, cudaStream_t s, bool pdl = false) {
+    return launch_k(drot::drot_step_async_kernel<K, S>, dim3(G), dim3(drot::kThreads), drot::AsyncLayout<K, S>::bytes,
+                    s, pdl, A);
 }
 
 template <int K, int S>
-cudaError_t launch_tma(int G, const drot::StepArgs &A, cudaStream_t s) {
-    drot::drot_step_tma_kernel<K, S><<<G, drot::kThreads + 32, drot::TmaLayout<K, S>::bytes, s>>>(A);
-    return cudaGetLastError();
+cudaError_t launch_tma(int G, const drot::StepArgs &A, cudaStream_t s, bool pdl = false) {
+    return launch_k(drot::drot_step_tma_kernel<K, S>, dim3(G), dim3(drot::kThreads + 32), drot::TmaLayout<K, S>::bytes,
+                    s, pdl, A);
 }
 
 }  // namespace
@@ -285,11 +358,11 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
     P.variant = variant;
     P.S = variant == 2 ? tma_stages(K) : (variant == 3 ? async_stages(K) : 0);
     P.accumulate = h->cfg.deterministic ? 0 : 1;
-    if (h->cfg.persistent) {
+    if (h->cfg.persistent || h->cfg.c_skip) {
         P.variant = variant = 1;
         P.S = 0;
-        P.accumulate = 1;
     }
+    if (h->cfg.persistent) P.accumulate = 1;
     int G = h->cfg.grid_ctas;
     if (G <= 0) {
         // as many CTAs as fit on the SMs at once (one wave); small problems use fewer
@@ -344,6 +417,7 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
         gi = (int)std::lround(2.0e-3 / t_iter);
         gi = std::max(1, std::min(gi, 256));
     }
+    if (h->cfg.c_skip) gi = std::max(2, gi + (gi & 1));  // whole (C-reading, C-free) pairs per replay
     P.graph_iters = gi;
 }
 
@@ -380,14 +454,14 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
     h->tile_slot = carve<int>(cur, P.T + 1);
     h->u = carve<double>(cur, m);
     h->v = carve<double>(cur, n);
-    h->acc = carve<double>(cur, 2);
+    h->acc = carve<double>(cur, 8);
     h->gsync = carve<drot::GridSync>(cur, 1);
     DROT_CUDA(h, cudaMemsetAsync(h->gsync, 0, sizeof(drot::GridSync), h->stream));
     if (P.accumulate) {
         // totals start at zero; every finish pass resets what it reads
         DROT_CUDA(h, cudaMemsetAsync(h->u, 0, sizeof(double) * m, h->stream));
         DROT_CUDA(h, cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream));
-        DROT_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * 2, h->stream));
+        DROT_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream));
     }
     DROT_CUDA(h, cudaMemcpyAsync(h->wbound, P.wbound.data(), sizeof(long long) * (P.G + 1), cudaMemcpyHostToDevice,
                                  h->stream));
@@ -453,28 +527,45 @@ drot::FinishArgs finish_args(const drot_handle *h, long long m, long long n, con
     return F;
 }
 
+// Register-fed step in a C-skipping mode (1: read X and C, store X - rho C; 2: read that array only).
+cudaError_t launch_step_cskip(const Plan &P, const drot::StepArgs &A, int cm, cudaStream_t s, bool pdl = false) {
+    const dim3 g(P.G), b(drot::kThreads);
+    if (cm == 1) {
+        switch (P.K) {
+            case 1: return launch_k(drot::drot_step_kernel<1, true, 1>, g, b, 0, s, pdl, A);
+            case 2: return launch_k(drot::drot_step_kernel<2, true, 1>, g, b, 0, s, pdl, A);
+            default: return launch_k(drot::drot_step_kernel<4, true, 1>, g, b, 0, s, pdl, A);
+        }
+    }
+    switch (P.K) {
+        case 1: return launch_k(drot::drot_step_kernel<1, true, 2>, g, b, 0, s, pdl, A);
+        case 2: return launch_k(drot::drot_step_kernel<2, true, 2>, g, b, 0, s, pdl, A);
+        default: return launch_k(drot::drot_step_kernel<4, true, 2>, g, b, 0, s, pdl, A);
+    }
+}
+
 template <bool UPDATE>
-cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s) {
+cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s, bool pdl = false) {
     if (UPDATE && P.variant == 3) {
         switch (P.K) {
-            case 1: return launch_async<1, 6>(P.G, A, s);
-            case 2: return launch_async<2, 4>(P.G, A, s);
-            default: return launch_async<4, 3>(P.G, A, s);
+            case 1: return launch_async<1, 6>(P.G, A, s, pdl);
+            case 2: return launch_async<2, 4>(P.G, A, s, pdl);
+            default: return launch_async<4, 3>(P.G, A, s, pdl);
         }
     }
     if (UPDATE && P.variant == 2) {
         switch (P.K) {
-            case 1: return launch_tma<1, 8>(P.G, A, s);
-            case 2: return launch_tma<2, 4>(P.G, A, s);
-            default: return launch_tma<4, 4>(P.G, A, s);
+            case 1: return launch_tma<1, 8>(P.G, A, s, pdl);
+            case 2: return launch_tma<2, 4>(P.G, A, s, pdl);
+            default: return launch_tma<4, 4>(P.G, A, s, pdl);
         }
     }
+    const dim3 g(P.G), b(drot::kThreads);
     switch (P.K) {
-        case 1: drot::drot_step_kernel<1, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
-        case 2: drot::drot_step_kernel<2, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
-        default: drot::drot_step_kernel<4, UPDATE><<<P.G, drot::kThreads, 0, s>>>(A); break;
+        case 1: return launch_k(drot::drot_step_kernel<1, UPDATE>, g, b, 0, s, pdl, A);
+        case 2: return launch_k(drot::drot_step_kernel<2, UPDATE>, g, b, 0, s, pdl, A);
+        default: return launch_k(drot::drot_step_kernel<4, UPDATE>, g, b, 0, s, pdl, A);
     }
-    return cudaGetLastError();
 }
 
 void destroy_graphs(drot_handle *h) {
@@ -503,13 +594,19 @@ drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, con
         // profile events per iteration: [3 it] before the step, [3 it + 1] between step and
         // finish, [3 it + 2] after the finish; [3 G] closes the last iteration
         for (int it = 0; it < P.graph_iters && err == cudaSuccess; ++it) {
+            const bool cskip = key.c_skip != 0;
             if (prof) err = cudaEventRecordWithFlags(h->ev[inst][3 * it], h->stream, cudaEventRecordExternal);
-            if (err == cudaSuccess) err = launch_step<true>(P, A, h->stream);
+            const bool pdl = !prof;  // an event record between kernels would break the programmatic edge
+            if (err == cudaSuccess)
+                err = cskip ? launch_step_cskip(P, A, (it & 1) ? 2 : 1, h->stream, pdl)
+                            : launch_step<true>(P, A, h->stream, pdl);
             if (prof && err == cudaSuccess)
                 err = cudaEventRecordWithFlags(h->ev[inst][3 * it + 1], h->stream, cudaEventRecordExternal);
             if (err == cudaSuccess) {
-                drot::drot_finish_kernel<<<P.fin_blocks, drot::kFinishThreads, 0, h->stream>>>(F);
-                err = cudaGetLastError();
+                drot::FinishArgs Fi = F;
+                Fi.no_test = (cskip && (it & 1)) ? 1 : 0;
+                err = launch_k(drot::drot_finish_kernel, dim3(P.fin_blocks), dim3(drot::kFinishThreads), 0, h->stream,
+                               pdl, Fi);
             }
             if (prof && err == cudaSuccess)
                 err = cudaEventRecordWithFlags(h->ev[inst][3 * it + 2], h->stream, cudaEventRecordExternal);
@@ -633,7 +730,51 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
 
     long long iters_done = 0;
     int done = max_iter > 0 ? drot::kRunning : drot::kIterCap;
-    if (max_iter > 0 && h->cfg.persistent) {
+    const ClusterPlan cp = cluster_plan(m, n);
+    // automatic: only when no setting asks for the streaming path explicitly
+    const bool explicit_stream = h->cfg.step_variant != 0 || h->cfg.tile_k != 0 || h->cfg.grid_ctas != 0 ||
+                                 h->cfg.persistent || h->cfg.deterministic || h->cfg.c_skip;
+    const bool use_cluster = cp.cs > 0 && !h->cfg.c_skip &&
+                             (h->cfg.cluster == 2 || (h->cfg.cluster == 0 && !explicit_stream));
+    if (h->cfg.cluster == 2 && !use_cluster)
+        return fail(h, DROT_ERR_INVALID_ARG, "a %lld x %lld problem does not fit on one cluster", m, n);
+    if (max_iter > 0 && use_cluster) {
+        // whole solve on one cluster; a launch runs up to `budget` iterations
+        drot::ClusterArgs ca{};
+        ca.C = C;
+        ca.X = X;
+        ca.p = p;
+        ca.q = q;
+        ca.g = h->g;
+        ca.h = h->h;
+        ca.a = h->a;
+        ca.b = h->b;
+        ca.sc = h->d_sc;
+        ca.m = m;
+        ca.n = n;
+        ca.ld = ld;
+        ca.rows_per_cta = cp.R;
+        ca.cols_per_cta = cp.Q;
+        ca.npad = cp.npad;
+        ca.inv_n = 1.0 / (double)n;
+        ca.inv_m = 1.0 / (double)m;
+        ca.inv_mn = 1.0 / (double)(m + n);
+        ca.budget = std::min<long long>(max_iter, 200000);
+        const long long max_launches = (max_iter + ca.budget - 1) / ca.budget + 2;
+        for (long long l = 0; l < max_launches; ++l) {
+            const cudaError_t e = cp.cs == 16 ? launch_cluster<16>(cp, ca, h->stream) : launch_cluster<8>(cp, ca, h->stream);
+            if (e != cudaSuccess) return fail(h, DROT_ERR_CUDA, "cluster launch failed: %s", cudaGetErrorString(e));
+            h->prof.kernel_launches += 1;
+            DROT_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (h->h_status->done != drot::kRunning) {
+                done = h->h_status->done;
+                break;
+            }
+        }
+        if (done == drot::kRunning) return fail(h, DROT_ERR_CUDA, "cluster iteration did not report completion");
+        h->prof.step_variant = 4;  // cluster-resident
+    } else if (max_iter > 0 && h->cfg.persistent) {
         // one cooperative launch runs up to `budget` iterations (about half a second of work)
         const double t_iter = 12.0 * (double)m * (double)n / 6.0e12 + 8.0e-6;
         const long long budget = std::max(1LL, std::min<long long>(max_iter, std::llround(0.5 / t_iter)));
@@ -666,6 +807,7 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
         key.arena = h->work.ptr; key.K = P.K; key.G = P.G; key.graph_iters = P.graph_iters;
         key.variant = P.variant;
         key.accumulate = P.accumulate;
+        key.c_skip = h->cfg.c_skip ? 1 : 0;
         key.profile = h->cfg.profile ? 1 : 0;
         if (!(key == h->key) || !h->exec[0]) {
             st = build_graphs(h, key, P, A, F);
@@ -735,6 +877,17 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
             return fail(h, DROT_ERR_CUDA, "iteration did not report completion after %lld replays", issued);
     }
 
+    if (h->cfg.c_skip && max_iter > 0) {
+        // after an odd number of passes the array holds X - rho C: restore X
+        DROT_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+        DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (h->h_status->k & 1) {
+            const int rblocks = (int)std::min<long long>(8LL * h->num_sms, std::max<long long>(1, (m * n + 255) / 256));
+            drot::drot_restore_plan_kernel<<<rblocks, 256, 0, h->stream>>>(X, C, m, n, ld, h->d_sc);
+            DROT_CUDA(h, cudaGetLastError());
+            h->prof.kernel_launches += 1;
+        }
+    }
     // outputs
     const int eblocks = (int)std::min<long long>(2LL * h->num_sms, std::max<long long>(1, (m + n + 255) / 256));
     drot::drot_export_duals_kernel<<<eblocks, 256, 0, h->stream>>>(h->g, h->h, h->d_sc, mu, nu, m, n, 1.0 / n,
@@ -754,8 +907,8 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     h->prof.grid_ctas = P.G;
     h->prof.col_tiles = P.T;
     h->prof.graph_iters = P.graph_iters;
-    h->prof.step_variant = P.variant;
-    h->prof.stages = P.S;
+    h->prof.step_variant = use_cluster && max_iter > 0 ? 4 : P.variant;
+    h->prof.stages = use_cluster && max_iter > 0 ? cp.cs : P.S;
 
     drot_status out = DROT_OK;
     if (done == drot::kIterCap) out = DROT_NOT_CONVERGED;
@@ -767,8 +920,8 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
         res->dual_obj = fin.dual;
         res->gap = fin.gap;
         res->res_l1 = fin.res_l1;
-        res->res_l2 = fin.res_l2;
-        res->dual_res = fin.dual_res_prev;
+        res->res_l2 = std::sqrt(fin.res_l2);         // the device keeps these two squared
+        res->dual_res = std::sqrt(fin.dual_res_prev);
         res->nnz = (int64_t)fin.nnz;
         res->status = out;
         if (iters_done == 0) {
@@ -921,7 +1074,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         P.h = carve<double>(cur, n);
         P.b = carve<double>(cur, n);
         P.v = carve<double>(cur, n);
-        P.acc = carve<double>(cur, 2);
+        P.acc = carve<double>(cur, 8);
         P.finpart = carve<double>(cur, (size_t)drot::kFinishAcc * P.fin_blocks);
         P.sc = d_sc + b;
         P.m = m;
@@ -1083,8 +1236,8 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
             R.dual_obj = c.dual;
             R.gap = c.gap;
             R.res_l1 = c.res_l1;
-            R.res_l2 = c.res_l2;
-            R.dual_res = c.dual_res_prev;
+            R.res_l2 = std::sqrt(c.res_l2);
+            R.dual_res = std::sqrt(c.dual_res_prev);
             R.nnz = (int64_t)c.nnz;
             R.status = status[b];
             R.seconds = 0.0;
@@ -1130,6 +1283,8 @@ void drot_config_default(drot_config *cfg) {
     cfg->deterministic = 0;
     cfg->autotune = 0;
     cfg->persistent = 0;
+    cfg->c_skip = 0;
+    cfg->cluster = 0;
 }
 
 drot_status drot_create(drot_handle **out, const drot_config *cfg) {
@@ -1144,6 +1299,7 @@ drot_status drot_create(drot_handle **out, const drot_config *cfg) {
         return DROT_ERR_CUDA;
     }
     if (c.device < 0 || c.device >= ndev) return DROT_ERR_INVALID_ARG;
+    if (c.c_skip) c.persistent = 0;
     drot_handle *h = new (std::nothrow) drot_handle();
     if (!h) return DROT_ERR_OOM;
     h->cfg = c;
@@ -1532,8 +1688,8 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
         res->dual_obj = st.dual;
         res->gap = st.gap;
         res->res_l1 = st.res_l1;
-        res->res_l2 = st.res_l2;
-        res->dual_res = st.dual_res_prev;
+        res->res_l2 = std::sqrt(st.res_l2);
+        res->dual_res = std::sqrt(st.dual_res_prev);
         res->nnz = (int64_t)st.nnz;
         res->status = out;
         if (st.k == 0) res->primal_obj = res->dual_obj = res->gap = res->res_l1 = res->res_l2 = res->dual_res = NAN;

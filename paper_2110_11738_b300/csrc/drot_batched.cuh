@@ -29,7 +29,7 @@ struct BatchProb {
     double* nu;
     double *g, *h, *a, *b;  // phi/psi numerators and the a, b state vectors
     double *u, *v;          // row / column totals (FP64 atomics), reset by the finish pass
-    double* acc;            // [2] <C,X> and sum [d]_+^2 (FP64 atomics)
+    double* acc;            // [8] <C,X>, sum [d]_+^2 and the finish totals (FP64 atomics)
     double* finpart;        // [fin_blocks][kFinishAcc]
     Scalars* sc;
     long long m, n, ld;

@@ -1,0 +1,297 @@
+// Cluster-resident DROT for small problems.
+//
+// One thread-block cluster of CS CTAs keeps the whole problem on chip: CTA r holds a
+// contiguous block of rows of X and C in its shared memory for the entire solve, so an
+// iteration of Algorithm 1 (Sec. 3.1) touches no global memory at all.  The row sums
+// are local to a CTA; column sums and the scalar totals are exchanged through
+// distributed shared memory (each CTA owns a range of columns and finishes steps 5-8
+// for its rows and its columns), and two hardware cluster barriers per iteration
+// order the exchange.  Every CTA then forms the same scalar totals in the same order,
+// so all CTAs take the same stopping decision and leave the loop together.
+//
+// Shared buffers written in one iteration and read remotely are double-buffered by
+// iteration parity: a CTA can overwrite buffer k & 1 only after the barrier of
+// iteration k + 1 that every CTA reaches after its last remote read of iteration k.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "drot_kernels.cuh"
+
+namespace drot {
+
+constexpr int kClusterThreads = 256;
+constexpr int kClusterParts = 8;  // sum r, ||.||_1, ||.||^2, p.g, q.h, sum s, <C,X>, sum [d]_+^2
+
+struct ClusterArgs {
+    const float* C;
+    float* X;
+    const double* p;
+    const double* q;
+    double *g, *h, *a, *b;  // state in global memory (read at entry, written at exit)
+    Scalars* sc;
+    long long m, n, ld;
+    int rows_per_cta;       // R: CTA r owns rows [r R, min(m, (r + 1) R))
+    int cols_per_cta;       // Q: CTA r owns columns [r Q, min(n, (r + 1) Q))
+    int npad;               // shared-memory row pitch (floats), a multiple of 4 >= n
+    long long budget;       // iterations this launch may run
+    double inv_n, inv_m, inv_mn;
+};
+
+struct ClusterSmem {
+    // carve of the dynamic shared memory of one CTA
+    float* Xs;      // [R][npad]
+    float* Cs;      // [R][npad]
+    float* psi;     // [npad]   psi_j (FP32) for all columns
+    double* colp;   // [2][n]   this CTA's column partials, by iteration parity
+    double* hown;   // [2][Q]   h_j of the owned columns (read remotely), by parity
+    double* part;   // [2][kClusterParts] this CTA's scalar partials, by parity
+    double* u;      // [R]      row sums of the owned rows
+    double* arow;   // [R]      a_i of the owned rows
+    double* grow;   // [R]      g_i of the owned rows
+    double* bcol;   // [Q]      b_j of the owned columns
+    double* hall;   // [n]      h_j of all columns
+    double* red;    // [kClusterThreads / 32][kClusterParts] block reduction scratch
+};
+
+__host__ __device__ inline size_t cluster_smem_bytes(int R, int Q, int npad, long long n) {
+    size_t b = 0;
+    b += 2 * (size_t)R * npad * sizeof(float);
+    b += (size_t)npad * sizeof(float);
+    b = (b + 15) / 16 * 16;
+    b += 2 * (size_t)n * sizeof(double) + 2 * (size_t)Q * sizeof(double) + 2 * kClusterParts * sizeof(double);
+    b += 2 * (size_t)R * sizeof(double) + (size_t)R * sizeof(double) + (size_t)Q * sizeof(double);
+    b += (size_t)n * sizeof(double) + (kClusterThreads / 32) * kClusterParts * sizeof(double);
+    return b;
+}
+
+__device__ inline ClusterSmem carve_cluster_smem(unsigned char* base, int R, int Q, int npad, long long n) {
+    ClusterSmem S;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* p = base + off;
+        off += bytes;
+        return p;
+    };
+    S.Xs = reinterpret_cast<float*>(take((size_t)R * npad * sizeof(float)));
+    S.Cs = reinterpret_cast<float*>(take((size_t)R * npad * sizeof(float)));
+    S.psi = reinterpret_cast<float*>(take((size_t)npad * sizeof(float)));
+    off = (off + 15) / 16 * 16;
+    S.colp = reinterpret_cast<double*>(take(2 * (size_t)n * sizeof(double)));
+    S.hown = reinterpret_cast<double*>(take(2 * (size_t)Q * sizeof(double)));
+    S.part = reinterpret_cast<double*>(take(2 * kClusterParts * sizeof(double)));
+    S.u = reinterpret_cast<double*>(take((size_t)R * sizeof(double)));
+    S.arow = reinterpret_cast<double*>(take((size_t)R * sizeof(double)));
+    S.grow = reinterpret_cast<double*>(take((size_t)R * sizeof(double)));
+    S.bcol = reinterpret_cast<double*>(take((size_t)Q * sizeof(double)));
+    S.hall = reinterpret_cast<double*>(take((size_t)n * sizeof(double)));
+    S.red = reinterpret_cast<double*>(take((kClusterThreads / 32) * kClusterParts * sizeof(double)));
+    return S;
+}
+
+template <int CS>
+__global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(ClusterArgs P) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int R = P.rows_per_cta, Q = P.cols_per_cta, npad = P.npad;
+    const long long m = P.m, n = P.n;
+    ClusterSmem S = carve_cluster_smem(smem_raw, R, Q, npad, n);
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long r0 = (long long)rank * R;
+    const int nrows = (int)max(0LL, min((long long)R, m - r0));
+    const long long c0 = (long long)rank * Q;
+    const int ncols = (int)max(0LL, min((long long)Q, n - c0));
+
+    // ---- load the owned rows of X and C, and the state, into shared memory
+    for (long long e = tid; e < (long long)nrows * n; e += kClusterThreads) {
+        const long long i = e / n, j = e - i * n;
+        S.Xs[i * npad + j] = P.X[(r0 + i) * P.ld + j];
+        S.Cs[i * npad + j] = P.C[(r0 + i) * P.ld + j];
+    }
+    for (int i = tid; i < nrows; i += kClusterThreads) {
+        S.arow[i] = P.a[r0 + i];
+        S.grow[i] = P.g[r0 + i];
+    }
+    for (int j = tid; j < ncols; j += kClusterThreads) S.bcol[j] = P.b[c0 + j];
+    for (long long j = tid; j < n; j += kClusterThreads) S.hall[j] = P.h[j];
+    const double rho = P.sc->rho, inv_rho = P.sc->inv_rho, tol = P.sc->tol;
+    const double sum_p = P.sc->sum_p, sum_q = P.sc->sum_q;
+    const long long max_iter = P.sc->max_iter;
+    const int rule = P.sc->stop_rule;
+    double alpha = P.sc->alpha, c = P.sc->c;
+    long long k = P.sc->k;
+    int done = P.sc->done;
+    double primal = P.sc->primal, dual = P.sc->dual, gap = P.sc->gap, res_l1 = P.sc->res_l1;
+    double res_l2_sq = P.sc->res_l2, dres_sq = P.sc->dual_res_prev, beta = P.sc->beta;
+    const float rhof = (float)rho;
+    __syncthreads();
+    for (long long j = tid; j < n; j += kClusterThreads) S.psi[j] = (float)((S.hall[j] + c) * P.inv_m);
+    __syncthreads();
+
+    for (long long it = 0; it < P.budget && done == kRunning; ++it) {
+        const int buf = (int)(it & 1);
+        double* colp = S.colp + (size_t)buf * n;
+        // ---- phase 1: step 4 on the owned rows, with row sums, column partials, <C,X>, dual residual
+        float scx = 0.f, sd = 0.f;
+        for (int i = warp; i < nrows; i += kClusterThreads / 32) {
+            const float phi = (float)((S.grow[i] + c) * P.inv_n);
+            float* xr = S.Xs + (size_t)i * npad;
+            const float* cr = S.Cs + (size_t)i * npad;
+            float rs = 0.f;
+            for (long long j = lane; j < n; j += 32) {
+                const float d = fmaf(-rhof, cr[j], phi + S.psi[j]);
+                const float xn = fmaxf(xr[j] + d, 0.f);
+                xr[j] = xn;
+                rs += xn;
+                scx = fmaf(cr[j], xn, scx);
+                const float dp = fmaxf(d, 0.f);
+                sd = fmaf(dp, dp, sd);
+            }
+            rs = warp_sum_f32(rs);
+            if (lane == 0) S.u[i] = (double)rs;
+        }
+        __syncthreads();
+        // column partials: thread per column; runs of 16 rows in FP32, promoted to FP64
+        // (FP64 has a long dependent latency on this GPU)
+        for (long long j = tid; j < n; j += kClusterThreads) {
+            double v = 0.0;
+            for (int i0 = 0; i0 < nrows; i0 += 16) {
+                float f = 0.f;
+                for (int i = i0; i < min(nrows, i0 + 16); ++i) f += S.Xs[(size_t)i * npad + j];
+                v += (double)f;
+            }
+            colp[j] = v;
+        }
+        // CTA totals of <C,X> and sum [d]_+^2 (warp sums in FP32, then FP64 across warps)
+        scx = warp_sum_f32(scx);
+        sd = warp_sum_f32(sd);
+        if (lane == 0) {
+            S.red[warp * kClusterParts + 0] = (double)scx;
+            S.red[warp * kClusterParts + 1] = (double)sd;
+        }
+        cluster.sync();  // #1: every CTA's column partials are ready
+
+        // ---- phase 2: steps 5-8 for the owned rows and columns, CTA partials of the totals
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // sum r, l1, l2^2, p.g, q.h, sum s
+        for (int i = tid; i < nrows; i += kClusterThreads) {
+            const double r = S.u[i] - P.p[r0 + i];
+            const double gn = S.arow[i] - 2.0 * r;
+            S.arow[i] -= r;
+            S.grow[i] = gn;
+            acc[0] += r;
+            acc[1] += fabs(r);
+            acc[2] += r * r;
+            acc[3] += P.p[r0 + i] * gn;
+        }
+        double* hown = S.hown + (size_t)buf * Q;
+        for (int jj = tid; jj < ncols; jj += kClusterThreads) {
+            const long long j = c0 + jj;
+            double v4[4] = {0.0, 0.0, 0.0, 0.0};  // four chains, combined in a fixed order
+#pragma unroll
+            for (int rr = 0; rr < CS; ++rr) v4[rr & 3] += cluster.map_shared_rank(colp, rr)[j];
+            const double v = (v4[0] + v4[1]) + (v4[2] + v4[3]);
+            const double s = v - P.q[j];
+            const double hn = S.bcol[jj] - 2.0 * s;
+            S.bcol[jj] -= s;
+            hown[jj] = hn;
+            acc[5] += s;
+            acc[1] += fabs(s);
+            acc[2] += s * s;
+            acc[4] += P.q[j] * hn;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q2 = 0; q2 < 6; ++q2) acc[q2] += __shfl_xor_sync(0xffffffffu, acc[q2], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q2 = 0; q2 < 6; ++q2) S.red[warp * kClusterParts + 2 + q2] = acc[q2];
+        __syncthreads();
+        double* part = S.part + (size_t)buf * kClusterParts;
+        if (tid < kClusterParts) {
+            double v = 0.0;
+            for (int w = 0; w < kClusterThreads / 32; ++w) v += S.red[w * kClusterParts + tid];
+            // part layout: 0 sum r, 1 l1, 2 l2^2, 3 p.g, 4 q.h, 5 sum s, 6 <C,X>, 7 sum [d]_+^2
+            const int dst = tid < 2 ? 6 + tid : tid - 2;
+            part[dst] = v;
+        }
+        cluster.sync();  // #2: every CTA's partials and owned h_j are ready
+
+        // ---- phase 3 (every CTA, identically): totals, scalars, stopping test, h of all columns
+        double tot[kClusterParts], tot2[kClusterParts];
+#pragma unroll
+        for (int q2 = 0; q2 < kClusterParts; ++q2) tot[q2] = tot2[q2] = 0.0;
+#pragma unroll
+        for (int rr = 0; rr < CS; ++rr) {
+            const double* rp = cluster.map_shared_rank(part, rr);
+#pragma unroll
+            for (int q2 = 0; q2 < kClusterParts; ++q2) {
+                if (rr & 1) tot2[q2] += rp[q2];
+                else tot[q2] += rp[q2];
+            }
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < kClusterParts; ++q2) tot[q2] += tot2[q2];
+        beta = tot[0] * P.inv_mn;
+        const double c_new = 2.0 * beta - alpha;
+        const double pphi = (tot[3] + c_new * sum_p) * P.inv_n;
+        const double qpsi = (tot[4] + c_new * sum_q) * P.inv_m;
+        primal = tot[6];
+        dual = (pphi + qpsi) * inv_rho;
+        gap = fabs(primal - dual);
+        res_l1 = tot[1];
+        res_l2_sq = tot[2];
+        dres_sq = tot[7] * inv_rho * inv_rho;
+        alpha -= beta;
+        c = c_new;
+        k += 1;
+        const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2_sq) &&
+                            isfinite(dres_sq) && isfinite(c_new) && isfinite(tot[5]);
+        const bool conv = tol >= 0.0 && (!(rule & 1) || gap <= tol) && (!(rule & 2) || res_l1 <= tol) &&
+                          (!(rule & 4) || dres_sq <= tol * tol);
+        if (!finite) done = kNonFinite;
+        else if (conv) done = kConverged;
+        else if (k >= max_iter) done = kIterCap;
+        // h of all columns from their owners, then psi for the next pass
+        for (long long j = tid; j < n; j += kClusterThreads) {
+            const int owner = (int)(j / Q);
+            S.hall[j] = cluster.map_shared_rank(S.hown + (size_t)buf * Q, owner)[j - (long long)owner * Q];
+        }
+        __syncthreads();
+        for (long long j = tid; j < n; j += kClusterThreads) S.psi[j] = (float)((S.hall[j] + c) * P.inv_m);
+        __syncthreads();
+    }
+
+    // ---- write the iterate and the state back; no CTA leaves while others may read its memory
+    for (long long e = tid; e < (long long)nrows * n; e += kClusterThreads) {
+        const long long i = e / n, j = e - i * n;
+        P.X[(r0 + i) * P.ld + j] = S.Xs[i * npad + j];
+    }
+    for (int i = tid; i < nrows; i += kClusterThreads) {
+        P.a[r0 + i] = S.arow[i];
+        P.g[r0 + i] = S.grow[i];
+    }
+    for (int j = tid; j < ncols; j += kClusterThreads) {
+        P.b[c0 + j] = S.bcol[j];
+        P.h[c0 + j] = S.hall[c0 + j];
+    }
+    if (rank == 0 && tid == 0) {
+        Scalars* sc = P.sc;
+        sc->alpha = alpha;
+        sc->c = c;
+        sc->k = k;
+        sc->beta = beta;
+        sc->primal = primal;
+        sc->dual = dual;
+        sc->gap = gap;
+        sc->res_l1 = res_l1;
+        sc->res_l2 = res_l2_sq;
+        sc->dual_res_prev = dres_sq;
+        sc->done = done;
+    }
+    cluster.sync();
+}
+
+}  // namespace drot

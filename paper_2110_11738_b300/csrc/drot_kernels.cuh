@@ -80,13 +80,18 @@ struct StepArgs {
     double* ctapart;            // [G][2]: <C,X> and sum [d]_+^2 per CTA
     double* u;                  // accumulation mode: row totals (m), added with FP64 atomics
     double* v;                  // accumulation mode: column totals (n)
-    double* acc;                // accumulation mode: [2] <C,X> and sum [d]_+^2
+    double* acc;                // accumulation mode: [8] <C,X>, sum [d]_+^2 (added here), finish totals
     int accumulate;             // 1: atomics into u, v, acc; 0: fixed-order partials
     const long long* wbound;    // [G+1] segment range of each CTA
     const int* slot_base;       // [G]   first slot of each CTA
     long long m, n, ld;
     double inv_n, inv_m;
 };
+
+// Programmatic dependent launch: wait until the preceding kernel of the stream has
+// completed and its writes are visible (returns at once when the kernel was not
+// launched as a programmatic dependent).
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ float warp_sum_f32(float v) {
 #pragma unroll
@@ -135,7 +140,11 @@ __device__ __forceinline__ float4 ld_stream_ro(const float* p) {
 
 // The fused DR pass (UPDATE = true) or a plain row/column-sum pass over X
 // (UPDATE = false, used once to initialise a_0 and b_0 from the stored X_0).
-template <int K, bool UPDATE>
+// C-load skipping (Claim 1, Sec. 3.3): CM = 0 is the plain pass; CM = 1 reads X and C
+// and stores W = x+ - rho c instead of x+; CM = 2 reads W (no C) and forms
+// x+ = [W + phi + psi]_+.  A CM = 1 / CM = 2 pair moves 12 + 8 bytes per entry;
+// <C,X> and the dual residual need C and are only produced by CM = 0 / 1 passes.
+template <int K, bool UPDATE, int CM = 0>
 __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
     constexpr int TW = 128 * K;
     __shared__ double s_col[kWarps][TW];
@@ -181,7 +190,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
             for (int kk = 0; kk < K; ++kk) {
                 if (col0 + kk * 128 + lane * 4 < n) {
                     xv[kk] = *reinterpret_cast<const float4*>(A.X + rowoff + kk * 128);
-                    if (UPDATE) cv[kk] = ld_stream_ro(A.C + rowoff + kk * 128);
+                    if (UPDATE && CM != 2) cv[kk] = ld_stream_ro(A.C + rowoff + kk * 128);
                 }
             }
             float rs = 0.f;
@@ -191,18 +200,21 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
                 if (j < n) {
                     float xs[4] = {xv[kk].x, xv[kk].y, xv[kk].z, xv[kk].w};
                     float cc[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (UPDATE) { cc[0] = cv[kk].x; cc[1] = cv[kk].y; cc[2] = cv[kk].z; cc[3] = cv[kk].w; }
+                    if (UPDATE && CM != 2) { cc[0] = cv[kk].x; cc[1] = cv[kk].y; cc[2] = cv[kk].z; cc[3] = cv[kk].w; }
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         if (j + e < n) {
                             float xn = xs[e];
-                            if (UPDATE) {
+                            if (UPDATE && CM == 2) {
+                                xn = fmaxf(xs[e] + (phi + psi[kk][e]), 0.f);  // xs holds W = X - rho C
+                                xs[e] = xn;
+                            } else if (UPDATE) {
                                 const float d = fmaf(-rho, cc[e], phi + psi[kk][e]);
                                 xn = fmaxf(xs[e] + d, 0.f);
                                 scx = fmaf(cc[e], xn, scx);
                                 const float dp = fmaxf(d, 0.f);
                                 sd = fmaf(dp, dp, sd);
-                                xs[e] = xn;
+                                xs[e] = CM == 1 ? fmaf(-rho, cc[e], xn) : xn;  // CM 1 stores W
                             }
                             rs += xn;
                             cacc[kk][e] += xn;
@@ -275,10 +287,28 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
     }
 }
 
-template <int K, bool UPDATE>
+template <int K, bool UPDATE, int CM = 0>
 __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
+    wait_for_predecessor();
     if (A.sc->done != kRunning) return;
-    step_body<K, UPDATE>(A, blockIdx.x);
+    step_body<K, UPDATE, CM>(A, blockIdx.x);
+}
+
+// X = W + rho C: restores the plan after a solve that stopped on a C-reading pass of
+// the C-skipping schedule (the array then holds W = X - rho C, rounded to FP32).  An
+// entry that was 0 comes back as the rounding error of rho c, at most 2^-24 rho c in
+// magnitude; results at or below 2^-22 rho c are therefore set to 0, so X stays
+// nonnegative and keeps its zeros.
+__global__ void drot_restore_plan_kernel(float* X, const float* C, long long m, long long n, long long ld,
+                                         const Scalars* sc) {
+    const float rho = (float)sc->rho;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < m * n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx / n, j = idx - i * n;
+        const float rc = rho * C[i * ld + j];
+        const float x = fmaf(rho, C[i * ld + j], X[i * ld + j]);
+        X[i * ld + j] = x > rc * 2.384185791015625e-07f ? x : 0.f;  // 2^-22
+    }
 }
 
 
@@ -374,6 +404,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
     __shared__ int s_abort;
     __shared__ uint32_t s_issued;
 
+    wait_for_predecessor();
     if (A.sc->done != kRunning) return;
 
     const int lane = threadIdx.x & 31;
@@ -605,6 +636,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
     double* s_col = reinterpret_cast<double*>(smem_raw);  // reused at the end of each tile
     __shared__ double s_red[kWarps][2];
 
+    wait_for_predecessor();
     if (A.sc->done != kRunning) return;
 
     const int lane = threadIdx.x & 31;
@@ -764,7 +796,8 @@ struct FinishArgs {
     const double* ctapart;
     double* u;              // accumulation mode: row totals, read and reset to 0
     double* v;              // accumulation mode: column totals, read and reset to 0
-    double* acc;            // accumulation mode: [2] <C,X>, sum [d]_+^2, read and reset
+    double* acc;            // accumulation mode: [8] <C,X>, sum [d]_+^2 and the six finish totals,
+                            // read and reset by the last block
     int accumulate;
     const int* tile_slot;   // [T+1] first slot of each column tile
     const double* p;
@@ -779,6 +812,7 @@ struct FinishArgs {
     int T, TW, G;
     double inv_n, inv_m;
     double inv_mn;          // 1 / (m + n)
+    int no_test;            // 1: the preceding pass had no C (C-skipping): <C,X> unknown, no stopping test
 };
 
 // Sum of `count` partials spaced `stride` apart, in a fixed order: four
@@ -844,6 +878,62 @@ __device__ __forceinline__ bool arrive_last(Scalars* sc, int nblk) {
 
 // Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1), executed by block
 // `blk` of the `nblk` blocks (of NT threads) that serve this problem.
+// Scalar part of the finish (one thread): steps 5-8's scalars and the stopping test
+// from the totals tot[0..5] (sum r, ||r||_1 + ||s||_1, ||r||^2 + ||s||^2, p.g', q.h',
+// sum s), <C,X> and sum [phi + psi - rho C]_+^2.  Norms are kept squared on the device
+// (the host takes the square roots it reports), so the test needs no FP64 sqrt.
+__device__ __forceinline__ void finish_scalars(const FinishArgs& A, const double* tot, double scx, double sdx) {
+    Scalars* sc = A.sc;
+    const double alpha = __ldcg(&sc->alpha);
+    const double beta = tot[0] * A.inv_mn;            // step 5
+    const double c_new = 2.0 * beta - alpha;           // steps 6-7 scalar term
+    const double pphi = (tot[3] + c_new * sc->sum_p) * A.inv_n;
+    const double qpsi = (tot[4] + c_new * sc->sum_q) * A.inv_m;
+    const double inv_rho = sc->inv_rho;
+    const double primal = A.no_test ? __ldcg(&sc->primal) : scx;
+    const double dual = (pphi + qpsi) * inv_rho;
+    const double gap = fabs(primal - dual);
+    const double res_l1 = tot[1];
+    const double res_l2_sq = tot[2];
+    const double dres_sq = sdx * inv_rho * inv_rho;
+    sc->alpha = alpha - beta;                          // step 8
+    sc->c = c_new;
+    sc->beta = beta;
+    if (!A.no_test) {
+        sc->primal = primal;
+        sc->dual = dual;
+        sc->gap = gap;
+        sc->res_l1 = res_l1;
+        sc->res_l2 = res_l2_sq;          // squared (see above)
+        sc->dual_res_prev = dres_sq;     // squared
+    }
+    const long long k = __ldcg(&sc->k) + 1;
+    sc->k = k;
+    const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2_sq) &&
+                        isfinite(dres_sq) && isfinite(c_new) && isfinite(tot[5]);
+    const int rule = sc->stop_rule;
+    const double tol = sc->tol;
+    const bool conv = !A.no_test && tol >= 0.0 && (!(rule & 1) || gap <= tol) && (!(rule & 2) || res_l1 <= tol) &&
+                      (!(rule & 4) || dres_sq <= tol * tol);
+    int done = kRunning;
+    if (__ldcg(&sc->fault)) done = kFault;
+    else if (!finite) done = kNonFinite;
+    else if (conv) done = kConverged;
+    else if (k >= sc->max_iter) done = kIterCap;
+    sc->counter = 0u;
+    __threadfence();
+    sc->done = done;
+}
+
+// Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1), executed by block
+// `blk` of the `nblk` blocks (of NT threads) that serve this problem.
+//
+// Accumulation mode: every warp reduces its six partial sums with shuffles and adds
+// them into FP64 totals (A.acc[2..7]) with atomics; the last block to arrive reads
+// the totals once.  Fixed-order mode: per-block partials (finpart) summed by the last
+// block in block order.  FP64 has a long dependent latency on this GPU, so the
+// accumulation path keeps the chain after the element work to one warp reduction,
+// one fence, one ticket and one read of the totals.
 template <int NT = kFinishThreads>
 __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nblk) {
     __shared__ double s_red[NT / 32][kFinishAcc];
@@ -877,6 +967,29 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
             acc[4] += A.q[j] * hn;
         }
     }
+    if (A.accumulate) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < kFinishAcc; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int c = 0; c < kFinishAcc; ++c) atomicAdd(A.acc + 2 + c, acc[c]);
+            __threadfence();
+        }
+        if (!arrive_last(sc, nblk)) return;
+        if (threadIdx.x == 0) {
+            double tot[kFinishAcc];
+#pragma unroll
+            for (int c = 0; c < kFinishAcc; ++c) tot[c] = __ldcg(A.acc + 2 + c);
+            const double scx = __ldcg(A.acc + 0), sdx = __ldcg(A.acc + 1);
+#pragma unroll
+            for (int c = 0; c < kFinishAcc + 2; ++c) A.acc[c] = 0.0;
+            finish_scalars(A, tot, scx, sdx);
+        }
+        return;
+    }
+
     block_sum_f64<kFinishAcc, NT>(acc, s_red);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -890,62 +1003,17 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
     for (int c = 0; c < kFinishAcc + 2; ++c) tot[c] = 0.0;
     for (int bidx = threadIdx.x; bidx < nblk; bidx += NT)
         for (int c = 0; c < kFinishAcc; ++c) tot[c] += __ldcg(A.finpart + bidx * kFinishAcc + c);
-    if (A.accumulate) {
-        if (threadIdx.x == 0) {
-            tot[kFinishAcc + 0] = __ldcg(A.acc + 0);
-            tot[kFinishAcc + 1] = __ldcg(A.acc + 1);
-            A.acc[0] = 0.0;
-            A.acc[1] = 0.0;
-        }
-    } else {
-        for (int bidx = threadIdx.x; bidx < A.G; bidx += NT) {
-            tot[kFinishAcc + 0] += __ldcg(A.ctapart + 2 * bidx + 0);
-            tot[kFinishAcc + 1] += __ldcg(A.ctapart + 2 * bidx + 1);
-        }
+    for (int bidx = threadIdx.x; bidx < A.G; bidx += NT) {
+        tot[kFinishAcc + 0] += __ldcg(A.ctapart + 2 * bidx + 0);
+        tot[kFinishAcc + 1] += __ldcg(A.ctapart + 2 * bidx + 1);
     }
     __shared__ double s_red2[NT / 32][kFinishAcc + 2];
     block_sum_f64<kFinishAcc + 2, NT>(tot, s_red2);
-    if (threadIdx.x == 0) {
-        const double alpha = __ldcg(&sc->alpha);
-        const double beta = tot[0] * A.inv_mn;            // step 5
-        const double c_new = 2.0 * beta - alpha;           // steps 6-7 scalar term
-        const double pphi = (tot[3] + c_new * sc->sum_p) * A.inv_n;
-        const double qpsi = (tot[4] + c_new * sc->sum_q) * A.inv_m;
-        const double inv_rho = sc->inv_rho;
-        const double primal = tot[kFinishAcc + 0];
-        const double dual = (pphi + qpsi) * inv_rho;
-        const double gap = fabs(primal - dual);
-        const double res_l1 = tot[1];
-        const double res_l2 = sqrt(tot[2]);
-        const double dres = sqrt(tot[kFinishAcc + 1]) * inv_rho;
-        sc->alpha = alpha - beta;                          // step 8
-        sc->c = c_new;
-        sc->beta = beta;
-        sc->primal = primal;
-        sc->dual = dual;
-        sc->gap = gap;
-        sc->res_l1 = res_l1;
-        sc->res_l2 = res_l2;
-        sc->dual_res_prev = dres;
-        const long long k = __ldcg(&sc->k) + 1;
-        sc->k = k;
-        const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2) &&
-                            isfinite(dres) && isfinite(c_new) && isfinite(tot[5]);
-        const int rule = sc->stop_rule;
-        const bool conv = (!(rule & 1) || gap <= sc->tol) && (!(rule & 2) || res_l1 <= sc->tol) &&
-                          (!(rule & 4) || dres <= sc->tol);
-        int done = kRunning;
-        if (__ldcg(&sc->fault)) done = kFault;
-        else if (!finite) done = kNonFinite;
-        else if (conv) done = kConverged;
-        else if (k >= sc->max_iter) done = kIterCap;
-        sc->counter = 0u;
-        __threadfence();
-        sc->done = done;
-    }
+    if (threadIdx.x == 0) finish_scalars(A, tot, tot[kFinishAcc + 0], tot[kFinishAcc + 1]);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs A) {
+    wait_for_predecessor();
     if (A.sc->done != kRunning) return;
     finish_body<kFinishThreads>(A, blockIdx.x, gridDim.x);
 }

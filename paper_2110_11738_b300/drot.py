@@ -53,7 +53,8 @@ class DrotConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("stop_rule", ctypes.c_int),
                 ("rho0", ctypes.c_double), ("graph_iters", ctypes.c_int), ("tile_k", ctypes.c_int),
                 ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int), ("step_variant", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("c_skip", ctypes.c_int), ("cluster", ctypes.c_int)]
 
 
 class DrotResult(ctypes.Structure):
@@ -164,7 +165,8 @@ STOP_DUAL_RES = 4
 def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = STOP_GAP | STOP_RES_L1,
                 rho0: float = 2.0, graph_iters: int = 0, tile_k: int = 0, grid_ctas: int = 0,
                 profile: bool = False, step_variant: int = 0, deterministic: bool = False,
-                autotune: bool = False, persistent: bool = False) -> int:
+                autotune: bool = False, persistent: bool = False, c_skip: bool = False,
+                cluster: int = 0) -> int:
     """Create a solver handle; returns the opaque handle as an int."""
     lib = load()
     cfg = DrotConfig()
@@ -181,6 +183,8 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
     cfg.deterministic = int(bool(deterministic))
     cfg.autotune = int(bool(autotune))
     cfg.persistent = int(bool(persistent))
+    cfg.c_skip = int(bool(c_skip))
+    cfg.cluster = int(cluster)
     h = ctypes.c_void_p()
     st = lib.drot_create(ctypes.byref(h), ctypes.byref(cfg))
     if st != DROT_OK:
