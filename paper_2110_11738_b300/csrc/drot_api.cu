@@ -92,8 +92,8 @@ cudaError_t set_async_attr() {
                                 (int)drot::AsyncLayout<K, S>::bytes);
 }
 
-// Ring depth of the async-copy-fed step per tile width (two CTAs per SM).
-int async_stages(int K) { return K == 4 ? 3 : (K == 2 ? 4 : 6); }
+// Ring depth of the async-copy-fed step per tile width: 96 KB of ring per CTA, two CTAs per SM.
+int async_stages(int K) { return K == 4 ? 3 : (K == 2 ? 6 : 12); }
 
 // Cluster-resident solve: cluster size and per-CTA shared memory for a problem, or 0
 // if it does not fit on one cluster.
@@ -146,8 +146,8 @@ cudaError_t set_kernel_attributes() {
     cudaError_t e = set_tma_attr<1, 8>();
     if (e == cudaSuccess) e = set_tma_attr<2, 4>();
     if (e == cudaSuccess) e = set_tma_attr<4, 4>();
-    if (e == cudaSuccess) e = set_async_attr<1, 6>();
-    if (e == cudaSuccess) e = set_async_attr<2, 4>();
+    if (e == cudaSuccess) e = set_async_attr<1, 12>();
+    if (e == cudaSuccess) e = set_async_attr<2, 6>();
     if (e == cudaSuccess) e = set_async_attr<4, 3>();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(drot::drot_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -269,7 +269,7 @@ cudaError_t fill_occupancy(drot_handle *h) {
     const int v[4][5] = {{0, 0, 0, 0, 0},
                          {0, ldg_occupancy<1>(), ldg_occupancy<2>(), 0, ldg_occupancy<4>()},
                          {0, tma_occupancy<1, 8>(), tma_occupancy<2, 4>(), 0, tma_occupancy<4, 4>()},
-                         {0, async_occupancy<1, 6>(), async_occupancy<2, 4>(), 0, async_occupancy<4, 3>()}};
+                         {0, async_occupancy<1, 12>(), async_occupancy<2, 6>(), 0, async_occupancy<4, 3>()}};
     for (int a = 0; a < 4; ++a)
         for (int k = 0; k < 5; ++k) {
             if (v[a][k] < 0) return cudaErrorUnknown;
@@ -548,8 +548,8 @@ template <bool UPDATE>
 cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s, bool pdl = false) {
     if (UPDATE && P.variant == 3) {
         switch (P.K) {
-            case 1: return launch_async<1, 6>(P.G, A, s, pdl);
-            case 2: return launch_async<2, 4>(P.G, A, s, pdl);
+            case 1: return launch_async<1, 12>(P.G, A, s, pdl);
+            case 2: return launch_async<2, 6>(P.G, A, s, pdl);
             default: return launch_async<4, 3>(P.G, A, s, pdl);
         }
     }
@@ -1169,12 +1169,10 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         DROT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t err = cudaSuccess;
         for (int it = 0; it < gi && err == cudaSuccess; ++it) {
-            drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(A);
-            err = cudaGetLastError();
-            if (err == cudaSuccess) {
-                drot::drot_batched_finish_kernel<<<FB, drot::kFinishThreads, 0, h->stream>>>(A);
-                err = cudaGetLastError();
-            }
+            err = launch_k(drot::drot_batched_step_kernel<true>, dim3(G), dim3(drot::kThreads), 0, h->stream, true, A);
+            if (err == cudaSuccess)
+                err = launch_k(drot::drot_batched_finish_kernel, dim3(FB), dim3(drot::kFinishThreads), 0, h->stream,
+                               true, A);
         }
         cudaError_t end = cudaStreamEndCapture(h->stream, &graph);
         if (err != cudaSuccess || end != cudaSuccess) {

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
     __shared__ double s_col[kWarps][128 * KMAX];
     __shared__ double s_red[kWarps][2];
 
+    wait_for_predecessor();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const long long w0 = B.wbound[blockIdx.x];
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
 
 // Steps 5-8 and the stopping test of every active problem (one block group each).
 __global__ void __launch_bounds__(kFinishThreads) drot_batched_finish_kernel(BatchArgs B) {
+    wait_for_predecessor();
     const int pi = B.fin_prob[blockIdx.x];
     if (pi < 0) return;
     const BatchProb& P = B.probs[pi];

@@ -219,41 +219,54 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
         }
         cluster.sync();  // #2: every CTA's partials and owned h_j are ready
 
-        // ---- phase 3 (every CTA, identically): totals, scalars, stopping test, h of all columns
-        double tot[kClusterParts], tot2[kClusterParts];
+        // ---- phase 3 (every CTA, identically): totals, scalars, stopping test, h of all columns.
+        // Warp 0 gathers the CS partials (lane r reads CTA r), reduces them with a fixed
+        // shuffle pattern and lane 0 updates the scalars; the same code on the same data in
+        // every CTA gives bitwise the same result everywhere.  Broadcast through shared memory.
+        __shared__ double s_bc[4];
+        __shared__ int s_done;
+        if (warp == 0) {
+            double t[kClusterParts];
+            const double* rp = cluster.map_shared_rank(part, lane < CS ? lane : 0);
 #pragma unroll
-        for (int q2 = 0; q2 < kClusterParts; ++q2) tot[q2] = tot2[q2] = 0.0;
+            for (int q2 = 0; q2 < kClusterParts; ++q2) t[q2] = lane < CS ? rp[q2] : 0.0;
 #pragma unroll
-        for (int rr = 0; rr < CS; ++rr) {
-            const double* rp = cluster.map_shared_rank(part, rr);
+            for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int q2 = 0; q2 < kClusterParts; ++q2) {
-                if (rr & 1) tot2[q2] += rp[q2];
-                else tot[q2] += rp[q2];
+                for (int q2 = 0; q2 < kClusterParts; ++q2) t[q2] += __shfl_down_sync(0xffffffffu, t[q2], o);
+            if (lane == 0) {
+                beta = t[0] * P.inv_mn;
+                const double c_new = 2.0 * beta - alpha;
+                const double pphi = (t[3] + c_new * sum_p) * P.inv_n;
+                const double qpsi = (t[4] + c_new * sum_q) * P.inv_m;
+                primal = t[6];
+                dual = (pphi + qpsi) * inv_rho;
+                gap = fabs(primal - dual);
+                res_l1 = t[1];
+                res_l2_sq = t[2];
+                dres_sq = t[7] * inv_rho * inv_rho;
+                alpha -= beta;
+                c = c_new;
+                const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2_sq) &&
+                                    isfinite(dres_sq) && isfinite(c_new) && isfinite(t[5]);
+                const bool conv = tol >= 0.0 && (!(rule & 1) || gap <= tol) && (!(rule & 2) || res_l1 <= tol) &&
+                                  (!(rule & 4) || dres_sq <= tol * tol);
+                int dn = kRunning;
+                if (!finite) dn = kNonFinite;
+                else if (conv) dn = kConverged;
+                else if (k + 1 >= max_iter) dn = kIterCap;
+                s_bc[0] = c;
+                s_bc[1] = alpha;
+                s_bc[2] = beta;
+                s_done = dn;
             }
         }
-#pragma unroll
-        for (int q2 = 0; q2 < kClusterParts; ++q2) tot[q2] += tot2[q2];
-        beta = tot[0] * P.inv_mn;
-        const double c_new = 2.0 * beta - alpha;
-        const double pphi = (tot[3] + c_new * sum_p) * P.inv_n;
-        const double qpsi = (tot[4] + c_new * sum_q) * P.inv_m;
-        primal = tot[6];
-        dual = (pphi + qpsi) * inv_rho;
-        gap = fabs(primal - dual);
-        res_l1 = tot[1];
-        res_l2_sq = tot[2];
-        dres_sq = tot[7] * inv_rho * inv_rho;
-        alpha -= beta;
-        c = c_new;
+        __syncthreads();
+        c = s_bc[0];
+        alpha = s_bc[1];
+        beta = s_bc[2];
+        done = s_done;
         k += 1;
-        const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2_sq) &&
-                            isfinite(dres_sq) && isfinite(c_new) && isfinite(tot[5]);
-        const bool conv = tol >= 0.0 && (!(rule & 1) || gap <= tol) && (!(rule & 2) || res_l1 <= tol) &&
-                          (!(rule & 4) || dres_sq <= tol * tol);
-        if (!finite) done = kNonFinite;
-        else if (conv) done = kConverged;
-        else if (k >= max_iter) done = kIterCap;
         // h of all columns from their owners, then psi for the next pass
         for (long long j = tid; j < n; j += kClusterThreads) {
             const int owner = (int)(j / Q);

@@ -210,7 +210,7 @@ def test_stop_rules_match_oracle(rule):
 @pytest.mark.parametrize("m,n", [(300, 2600), (1000, 200)])
 def test_autotune_picks_a_plan_and_keeps_parity(m, n):
     pr = workloads.make_problem("plain_8192x6144", seed=m + n, m=m, n=n)
-    with drot.Solver(device=0, autotune=True) as s:
+    with drot.Solver(device=0, autotune=True, cluster=1) as s:
         _step_parity(s, pr, 2, seed=5)
         prof = s.profile()
         assert prof["step_variant"] in (1, 2, 3) and prof["tile_k"] in (1, 2, 4)
