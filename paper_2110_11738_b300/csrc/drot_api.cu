@@ -57,6 +57,32 @@ struct Arena {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Cost model of the CTA work split over row segments (one row of one column tile).
+// A warp takes one row segment per memory round trip whatever the segment's width, so
+// a segment of w columns costs w + kRowTripCost * TW column-equivalents: its bytes
+// plus a fixed share for the round trip.  Balancing by columns alone would hand the m
+// rows of a ragged last tile of a few columns (n = 20000 leaves 32 after 39 tiles of
+// 512) to one CTA, whose m / 8 round trips per warp would then set the step's length
+// (measured on B300: 1.7 TB/s at 20000 x 20000).  3.0 was the best of 0.25 .. 8 and
+// pure row-count balancing over square, wide, tall and ragged shapes (6.1 TB/s there).
+constexpr double kRowTripCost = 3.0;
+
+struct SegCost {
+    long long m, T, TW, last_w;
+    double full, last;  // cost of one row segment of a full tile / of the last tile
+    SegCost(long long m_, long long T_, long long TW_, long long n)
+        : m(m_), T(T_), TW(TW_), last_w(n - (T_ - 1) * TW_),
+          full((1.0 + kRowTripCost) * (double)TW_), last((double)last_w + kRowTripCost * (double)TW_) {}
+    double total() const { return (double)((T - 1) * m) * full + (double)m * last; }
+    // The number of leading segments (tile-major order) whose total cost is closest to `cost`.
+    long long units_for(double cost) const {
+        const double full_cost = (double)((T - 1) * m) * full;
+        const long long u = cost <= full_cost ? (long long)std::llround(cost / full)
+                                              : (T - 1) * m + (long long)std::llround((cost - full_cost) / last);
+        return std::min(std::max<long long>(u, 0), T * m);
+    }
+};
+
 // Ring depth of the TMA-fed step for a tile width (each stage holds 8 rows of X and C).
 // K = 4 rings take 160 KB (one CTA per SM); K = 2 and K = 1 rings fit two CTAs per SM.
 int tma_stages(int K) { return K == 4 ? 4 : (K == 2 ? 4 : 8); }
@@ -260,7 +286,6 @@ struct drot_handle {
     Arena batch;                        // per-problem vectors, scalars and work lists
     Scalars *h_bstat = nullptr;         // pinned read-back of every problem's scalars
     size_t h_bstat_cap = 0;
-    cudaGraphExec_t bexec = nullptr;
     int batch_k_thresholds[2] = {0, 0};  // autotuned tile policy: K = 1 below t0, 2 below t1, else 4
 };
 
@@ -332,9 +357,9 @@ bool is_device_ptr(const void *p, int device) {
 }
 
 // Choose the tile width, the grid and the per-CTA segment ranges.  Segment
-// ranges are balanced by the number of columns they cover (a ragged last tile
-// costs less per row), and slots are numbered in CTA order, which is also
-// column-tile order.
+// ranges are balanced by SegCost (a row of a ragged last tile costs less than a
+// full one, but not in proportion to its width), and slots are numbered in CTA
+// order, which is also column-tile order.
 void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int force_variant = 0, int force_k = 0) {
     int K = force_k ? force_k : h->cfg.tile_k;
     int variant = force_variant ? force_variant : h->cfg.step_variant;
@@ -376,18 +401,10 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
     if (h->cfg.persistent) G = std::min(G, std::max(1, h->occ_persistent[K]) * h->num_sms);
     P.G = G;
 
-    const long long last_w = n - (long long)(P.T - 1) * P.TW;  // columns of the last tile
-    const long long full_units = (long long)(P.T - 1) * m;
-    const double total_cost = (double)full_units * P.TW + (double)m * last_w;
-    auto units_for_cost = [&](double cost) -> long long {
-        const double full_cost = (double)full_units * P.TW;
-        long long u;
-        if (cost <= full_cost) u = (long long)std::llround(cost / P.TW);
-        else u = full_units + (long long)std::llround((cost - full_cost) / (double)last_w);
-        return std::min(std::max<long long>(u, 0), units);
-    };
+    const SegCost cost(m, P.T, P.TW, n);
+    const double total_cost = cost.total();
     P.wbound.assign(G + 1, 0);
-    for (int g = 1; g < G; ++g) P.wbound[g] = std::max(P.wbound[g - 1], units_for_cost(total_cost * g / G));
+    for (int g = 1; g < G; ++g) P.wbound[g] = std::max(P.wbound[g - 1], cost.units_for(total_cost * g / G));
     P.wbound[G] = units;
 
     P.slot_base.assign(G, 0);
@@ -945,7 +962,7 @@ struct BatchLists {
 // Tile width policy: K = 1 for n < t0, 2 for n < t1, else 4.
 int batch_k(long long n, const int thr[2]) { return n < thr[0] ? 1 : (n < thr[1] ? 2 : 4); }
 
-// Segment list, byte-balanced CTA ranges and finish-block groups of the active problems.
+// Segment list, cost-balanced CTA ranges (SegCost) and finish-block groups of the active problems.
 void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector<int> &active, int G, int FB,
                        BatchLists &L) {
     L.active = active;
@@ -954,11 +971,9 @@ void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector
     std::vector<double> cost0(na + 1, 0.0);
     for (int a = 0; a < na; ++a) {
         const drot::BatchProb &P = hp[active[a]];
-        const long long TW = 128LL * P.K;
         const long long units = (long long)P.T * P.m;
-        const long long last_w = P.n - (long long)(P.T - 1) * TW;
         L.unit0[a + 1] = L.unit0[a] + units;
-        cost0[a + 1] = cost0[a] + (double)(P.T - 1) * P.m * TW + (double)P.m * last_w;
+        cost0[a + 1] = cost0[a] + SegCost(P.m, P.T, 128LL * P.K, P.n).total();
     }
     const long long total = L.unit0[na];
     L.wbound.assign(G + 1, total);
@@ -970,14 +985,7 @@ void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector
         long long u = total;
         if (na > 0) {
             const drot::BatchProb &P = hp[active[a]];
-            const long long TW = 128LL * P.K;
-            const long long last_w = P.n - (long long)(P.T - 1) * TW;
-            const double full = (double)(P.T - 1) * P.m * TW;
-            const double lc = target - cost0[a];
-            long long lu = lc <= full ? (long long)std::llround(lc / TW)
-                                      : (long long)(P.T - 1) * P.m + (long long)std::llround((lc - full) / (double)last_w);
-            lu = std::min(std::max<long long>(lu, 0), (long long)P.T * P.m);
-            u = L.unit0[a] + lu;
+            u = L.unit0[a] + SegCost(P.m, P.T, 128LL * P.K, P.n).units_for(target - cost0[a]);
         }
         L.wbound[g] = std::max(L.wbound[g - 1], std::min(u, total));
     }
@@ -1155,54 +1163,88 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     DROT_CUDA(h, cudaGetLastError());
     h->prof.kernel_launches += 2;
 
-    // graph of `gi` iterations over the active list
-    double bytes_iter = 0.0;
-    for (int b : valid) bytes_iter += 12.0 * (double)pr[b].m * (double)pr[b].n;
-    int gi = h->cfg.graph_iters;
-    if (gi <= 0) gi = (int)std::max(1L, std::min(256L, std::lround(4.0e-3 / (bytes_iter / 6.0e12 + 12.0e-6))));
-    if (h->bexec) {
-        cudaGraphExecDestroy(h->bexec);
-        h->bexec = nullptr;
-    }
-    if (max_iter > 0 && nvalid > 0) {
+    // Graph replays of gi iterations over the active list.  gi follows the work still
+    // active (about 4 ms per replay, a power of 4 up to 256), so the replays stay long
+    // enough to hide the host round trip as problems converge; one graph per gi.
+    std::vector<std::pair<int, cudaGraphExec_t>> graphs;
+    auto release = [&]() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        graphs.clear();
+    };
+    auto pick_gi = [&](const std::vector<int> &act) {
+        if (h->cfg.graph_iters > 0) return h->cfg.graph_iters;
+        double bytes = 0.0;
+        for (int b : act) bytes += 12.0 * (double)pr[b].m * (double)pr[b].n;
+        const double want = 4.0e-3 / (bytes / 6.0e12 + 12.0e-6);
+        int g = 1;
+        while (g < 256 && 4.0 * g <= want) g *= 4;
+        return g;
+    };
+    auto graph_for = [&](int g, cudaGraphExec_t *out) -> drot_status {
+        for (auto &e : graphs)
+            if (e.first == g) {
+                *out = e.second;
+                return DROT_OK;
+            }
         cudaGraph_t graph = nullptr;
         DROT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t err = cudaSuccess;
-        for (int it = 0; it < gi && err == cudaSuccess; ++it) {
+        for (int it = 0; it < g && err == cudaSuccess; ++it) {
             err = launch_k(drot::drot_batched_step_kernel<true>, dim3(G), dim3(drot::kThreads), 0, h->stream, true, A);
             if (err == cudaSuccess)
                 err = launch_k(drot::drot_batched_finish_kernel, dim3(FB), dim3(drot::kFinishThreads), 0, h->stream,
                                true, A);
         }
-        cudaError_t end = cudaStreamEndCapture(h->stream, &graph);
-        if (err != cudaSuccess || end != cudaSuccess) {
+        cudaError_t endc = cudaStreamEndCapture(h->stream, &graph);
+        if (err != cudaSuccess || endc != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             return fail(h, DROT_ERR_CUDA, "batched graph capture failed: %s",
-                        cudaGetErrorString(err != cudaSuccess ? err : end));
+                        cudaGetErrorString(err != cudaSuccess ? err : endc));
         }
-        cudaError_t ie = cudaGraphInstantiate(&h->bexec, graph, 0);
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess)
             return fail(h, DROT_ERR_CUDA, "batched graph instantiate failed: %s", cudaGetErrorString(ie));
-
+        graphs.emplace_back(g, exec);
+        *out = exec;
+        return DROT_OK;
+    };
+    if (max_iter > 0 && nvalid > 0) {
         std::vector<int> active = valid;
-        const long long max_replays = (max_iter + gi - 1) / gi + 2;
+        const long long max_replays = max_iter + 2;  // every replay advances every active problem
         for (long long r = 0; r < max_replays && !active.empty(); ++r) {
-            DROT_CUDA(h, cudaGraphLaunch(h->bexec, h->stream));
+            const int gi = pick_gi(active);
+            cudaGraphExec_t exec = nullptr;
+            st = graph_for(gi, &exec);
+            if (st != DROT_OK) {
+                release();
+                return st;
+            }
+            cudaError_t e = cudaGraphLaunch(exec, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->h_bstat, d_sc, sizeof(Scalars) * B, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) {
+                release();
+                return fail(h, DROT_ERR_CUDA, "batched replay failed: %s", cudaGetErrorString(e));
+            }
             h->prof.graph_replays += 1;
             h->prof.kernel_launches += 2LL * gi;
-            DROT_CUDA(h, cudaMemcpyAsync(h->h_bstat, d_sc, sizeof(Scalars) * B, cudaMemcpyDeviceToHost, h->stream));
-            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
             std::vector<int> still;
             for (int b : active)
                 if (h->h_bstat[b].done == drot::kRunning) still.push_back(b);
             if (still.size() != active.size() && !still.empty()) {
                 build_batch_lists(hp, still, G, FB, L);
                 st = upload_lists(h, L, D, FB);
-                if (st != DROT_OK) return st;
+                if (st != DROT_OK) {
+                    release();
+                    return st;
+                }
             }
             active.swap(still);
         }
+        release();
         if (!active.empty())
             return fail(h, DROT_ERR_CUDA, "%zu problems did not report completion", active.size());
     }
@@ -1333,7 +1375,6 @@ drot_status drot_destroy(drot_handle *h) {
     if (h->tune_x.ptr) cudaFree(h->tune_x.ptr);
     if (h->batch.ptr) cudaFree(h->batch.ptr);
     if (h->h_bstat) cudaFreeHost(h->h_bstat);
-    if (h->bexec) cudaGraphExecDestroy(h->bexec);
     if (h->staging.ptr) cudaFree(h->staging.ptr);
     if (h->d_sc) cudaFree(h->d_sc);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -1543,17 +1584,10 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
     long long *wbound = g_static_wbound;
     int *slot_base = g_static_slot_base;
     int *tile_slot = g_static_tile_slot;
-    const long long last_w = n - (T - 1) * TW;
-    const double full_cost = (double)((T - 1) * m) * TW;
-    const double total_cost = full_cost + (double)m * last_w;
+    const SegCost cost(m, T, TW, n);
+    const double total_cost = cost.total();
     wbound[0] = 0;
-    for (int g = 1; g < G; ++g) {
-        const double cost = total_cost * g / G;
-        long long u = cost <= full_cost ? (long long)std::llround(cost / TW)
-                                        : (T - 1) * m + (long long)std::llround((cost - full_cost) / (double)last_w);
-        u = std::min(std::max<long long>(u, 0), units);
-        wbound[g] = std::max(wbound[g - 1], u);
-    }
+    for (int g = 1; g < G; ++g) wbound[g] = std::max(wbound[g - 1], cost.units_for(total_cost * g / G));
     wbound[G] = units;
     int slots = 0;
     for (long long t = 0; t <= T; ++t) tile_slot[t] = -1;

@@ -6,7 +6,7 @@
 // does (same per-entry arithmetic, same FP64 totals in accumulation mode, its own
 // scalar state, stopping test and flag).  What is shared is the launch: the row
 // segments of all active problems form one list (problem-major, then tile-major,
-// then row), the host cuts that list into one contiguous, byte-balanced range per
+// then row), the host cuts that list into one contiguous, cost-balanced range per
 // CTA, and each CTA walks its range segment by segment, taking the tile width of
 // the problem a segment belongs to.  The finish launch gives each active problem
 // its own group of blocks; the last block of a group closes that problem's
