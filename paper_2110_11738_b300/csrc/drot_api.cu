@@ -65,21 +65,37 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // 512) to one CTA, whose m / 8 round trips per warp would then set the step's length
 // (measured on B300: 1.7 TB/s at 20000 x 20000).  3.0 was the best of 0.25 .. 8 and
 // pure row-count balancing over square, wide, tall and ragged shapes (6.1 TB/s there).
+// Entering a tile costs a CTA kTileSwitchRows full rows more: the column partials of
+// the tile it leaves are reduced and flushed, and its copy pipeline drains and refills
+// (CTAs whose range crossed a tile boundary were the last to finish, by about 5 us).
 constexpr double kRowTripCost = 3.0;
+constexpr double kTileSwitchRows = 32.0;
 
 struct SegCost {
     long long m, T, TW, last_w;
-    double full, last;  // cost of one row segment of a full tile / of the last tile
+    double full, last, sw;  // cost of a row segment of a full tile / of the last tile; of a tile start
     SegCost(long long m_, long long T_, long long TW_, long long n)
         : m(m_), T(T_), TW(TW_), last_w(n - (T_ - 1) * TW_),
-          full((1.0 + kRowTripCost) * (double)TW_), last((double)last_w + kRowTripCost * (double)TW_) {}
-    double total() const { return (double)((T - 1) * m) * full + (double)m * last; }
-    // The number of leading segments (tile-major order) whose total cost is closest to `cost`.
+          full((1.0 + kRowTripCost) * (double)TW_), last((double)last_w + kRowTripCost * (double)TW_),
+          sw(kTileSwitchRows * full) {}
+    // Cost of the first u segments (tile-major order).
+    double before(long long u) const {
+        const long long full_units = (T - 1) * m;
+        const double rows = u <= full_units ? (double)u * full
+                                            : (double)full_units * full + (double)(u - full_units) * last;
+        return rows + (double)((u + m - 1) / m) * sw;
+    }
+    double total() const { return before(T * m); }
+    // The number of leading segments whose cost is closest to `cost`.
     long long units_for(double cost) const {
-        const double full_cost = (double)((T - 1) * m) * full;
-        const long long u = cost <= full_cost ? (long long)std::llround(cost / full)
-                                              : (T - 1) * m + (long long)std::llround((cost - full_cost) / last);
-        return std::min(std::max<long long>(u, 0), T * m);
+        long long lo = 0, hi = T * m;  // before() is increasing: find the first u with before(u) >= cost
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (before(mid) < cost) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo > 0 && cost - before(lo - 1) < before(lo) - cost) --lo;
+        return lo;
     }
 };
 
@@ -453,7 +469,9 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
                          align_up(sizeof(double) * drot::kFinishAcc * P.fin_blocks, 256) +
                          align_up(sizeof(long long) * (P.G + 1), 256) + align_up(sizeof(int) * P.G, 256) +
                          align_up(sizeof(int) * (P.T + 1), 256) + align_up(sizeof(double) * m, 256) +
-                         align_up(sizeof(double) * n, 256) + 256 + align_up(sizeof(drot::GridSync), 256) + 4096;
+                         align_up(sizeof(double) * n, 256) +
+                         align_up(sizeof(double) * drot::kAccSlots * drot::kAccStride, 256) +
+                         align_up(sizeof(drot::GridSync), 256) + 4096;
     drot_status st = arena_reserve(h, h->work, bytes);
     if (st != DROT_OK) return st;
     char *cur = static_cast<char *>(h->work.ptr);
@@ -471,14 +489,14 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
     h->tile_slot = carve<int>(cur, P.T + 1);
     h->u = carve<double>(cur, m);
     h->v = carve<double>(cur, n);
-    h->acc = carve<double>(cur, 8);
+    h->acc = carve<double>(cur, (size_t)drot::kAccSlots * drot::kAccStride);
     h->gsync = carve<drot::GridSync>(cur, 1);
     DROT_CUDA(h, cudaMemsetAsync(h->gsync, 0, sizeof(drot::GridSync), h->stream));
     if (P.accumulate) {
         // totals start at zero; every finish pass resets what it reads
         DROT_CUDA(h, cudaMemsetAsync(h->u, 0, sizeof(double) * m, h->stream));
         DROT_CUDA(h, cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream));
-        DROT_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * 8, h->stream));
+        DROT_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * drot::kAccSlots * drot::kAccStride, h->stream));
     }
     DROT_CUDA(h, cudaMemcpyAsync(h->wbound, P.wbound.data(), sizeof(long long) * (P.G + 1), cudaMemcpyHostToDevice,
                                  h->stream));
@@ -1045,7 +1063,8 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         hp[b].fin_blocks = fb;
         FB += fb;
         off[b] = bytes;
-        bytes += align_up(sizeof(double) * m, 256) * 3 + align_up(sizeof(double) * n, 256) * 3 + 256 +
+        bytes += align_up(sizeof(double) * m, 256) * 3 + align_up(sizeof(double) * n, 256) * 3 +
+                 align_up(sizeof(double) * drot::kAccSlots * drot::kAccStride, 256) +
                  align_up(sizeof(double) * drot::kFinishAcc * fb, 256);
     }
     const size_t vec_bytes = bytes - align_up(sizeof(Scalars) * B, 256);
@@ -1082,7 +1101,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         P.h = carve<double>(cur, n);
         P.b = carve<double>(cur, n);
         P.v = carve<double>(cur, n);
-        P.acc = carve<double>(cur, 8);
+        P.acc = carve<double>(cur, (size_t)drot::kAccSlots * drot::kAccStride);
         P.finpart = carve<double>(cur, (size_t)drot::kFinishAcc * P.fin_blocks);
         P.sc = d_sc + b;
         P.m = m;

@@ -214,8 +214,8 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
             double v2[2] = {scx64, sd64};
             block_sum_f64<2, kThreads>(v2, s_red);  // ends with a block barrier
             if (threadIdx.x == 0) {
-                atomicAdd(P.acc + 0, v2[0]);
-                atomicAdd(P.acc + 1, v2[1]);
+                atomicAdd(acc_at(P.acc, 0), v2[0]);
+                atomicAdd(acc_at(P.acc, 1), v2[1]);
             }
         } else {
             __syncthreads();

@@ -45,6 +45,12 @@ constexpr int kFlushRows = 16;  // rows per warp between FP32 -> FP64 promotions
 // small fraction of its FP32 rate) spreads over every SM.
 constexpr int kFinishThreads = 64;
 constexpr int kFinishAcc = 6;
+// The FP64 totals of accumulation mode (<C,X>, sum [d]_+^2 and the six finish totals)
+// sit one per 128-byte line, so that the atomics aimed at different totals are spread
+// over L2 slices instead of queueing on one.
+constexpr int kAccSlots = 8;
+constexpr int kAccStride = 16;
+__device__ __forceinline__ double* acc_at(double* acc, int c) { return acc + c * kAccStride; }
 
 enum DoneCode : int { kRunning = 0, kConverged = 1, kIterCap = 2, kNonFinite = 3, kFault = 4 };
 
@@ -92,6 +98,9 @@ struct StepArgs {
 // completed and its writes are visible (returns at once when the kernel was not
 // launched as a programmatic dependent).
 __device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the stream (launched as a programmatic dependent) start its
+// blocks now; it still waits in griddepcontrol.wait for this whole grid to finish.
+__device__ __forceinline__ void release_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ float warp_sum_f32(float v) {
 #pragma unroll
@@ -277,8 +286,8 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
         block_sum_f64<2, kThreads>(v, s_red);
         if (threadIdx.x == 0) {
             if (A.accumulate) {
-                atomicAdd(A.acc + 0, v[0]);
-                atomicAdd(A.acc + 1, v[1]);
+                atomicAdd(acc_at(A.acc, 0), v[0]);
+                atomicAdd(acc_at(A.acc, 1), v[1]);
             } else {
                 A.ctapart[2 * cta + 0] = v[0];
                 A.ctapart[2 * cta + 1] = v[1];
@@ -583,8 +592,8 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
     block_sum_f64<2, kThreads + 32>(v, s_red);
     if (threadIdx.x == 0) {
         if (A.accumulate) {
-            atomicAdd(A.acc + 0, v[0]);
-            atomicAdd(A.acc + 1, v[1]);
+            atomicAdd(acc_at(A.acc, 0), v[0]);
+            atomicAdd(acc_at(A.acc, 1), v[1]);
         } else {
             A.ctapart[2 * blockIdx.x + 0] = v[0];
             A.ctapart[2 * blockIdx.x + 1] = v[1];
@@ -628,6 +637,29 @@ struct AsyncLayout {
                                         : (size_t)kWarps * TW * sizeof(double);
 };
 
+// Copies row r of this warp's rows in the tile (row first + kWarps r, if r < nr) of X
+// and C into ring stage r mod S, and commits a group (empty past the last row, which
+// keeps the group count in step).
+template <int K, int S>
+__device__ __forceinline__ void async_issue_row(const StepArgs& A, float* ring, long long first, int nr,
+                                                long long col0, int lane, int r) {
+    constexpr int TW = 128 * K;
+    if (r < nr) {
+        const long long i = first + (long long)kWarps * r;
+        float* xs = ring + (size_t)(r % S) * 2 * TW;
+        float* cs_ = xs + TW;
+        const long long rowoff = i * A.ld + col0 + lane * 4;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            if (col0 + kk * 128 + lane * 4 < A.n) {
+                cp_async16(xs + kk * 128 + lane * 4, A.X + rowoff + kk * 128);
+                cp_async16(cs_ + kk * 128 + lane * 4, A.C + rowoff + kk * 128);
+            }
+        }
+    }
+    cp_async_commit();
+}
+
 template <int K, int S>
 __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A) {
     constexpr int TW = 128 * K;
@@ -636,14 +668,32 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
     double* s_col = reinterpret_cast<double*>(smem_raw);  // reused at the end of each tile
     __shared__ double s_red[kWarps][2];
 
-    wait_for_predecessor();
-    if (A.sc->done != kRunning) return;
-
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const long long m = A.m, n = A.n, ld = A.ld;
     const long long w0 = A.wbound[blockIdx.x];
     const long long w1 = A.wbound[blockIdx.x + 1];
+
+    // The copies of the first S - 1 rows go out before the wait for the preceding
+    // finish kernel: X and C are final once that kernel runs (it waited for the step
+    // before it), and what it writes (g, h, the scalars, the zeroed totals) is read or
+    // accumulated only after the wait.  A solve that has already stopped skips them.
+    bool primed = false;
+    if (w0 < w1 && __ldcg(&A.sc->done) == kRunning) {
+        const long long t = w0 / m;
+        const long long i0 = w0 - t * m, i1 = min(w1, (t + 1) * m) - t * m;
+        const long long first = i0 + warp;
+        const int nr = first < i1 ? (int)((i1 - 1 - first) / kWarps + 1) : 0;
+#pragma unroll
+        for (int r = 0; r < S - 1; ++r) async_issue_row<K, S>(A, ring, first, nr, t * TW, lane, r);
+        primed = true;
+    }
+    wait_for_predecessor();
+    if (A.sc->done != kRunning) {
+        cp_async_wait<0>();  // let the early copies land before the block's shared memory is released
+        return;
+    }
+
     const float rho = (float)A.sc->rho;
     const double cs = A.sc->c;
     int slot = A.slot_base[blockIdx.x];
@@ -670,24 +720,12 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
         // rows of this warp in the tile: i0 + warp + kWarps * r, r = 0 .. nr-1
         const long long first = i0 + warp;
         const int nr = first < i1 ? (int)((i1 - 1 - first) / kWarps + 1) : 0;
-        auto issue = [&](int r) {
-            if (r < nr) {
-                const long long i = first + (long long)kWarps * r;
-                float* xs = ring + (size_t)(r % S) * 2 * TW;
-                float* cs_ = xs + TW;
-                const long long rowoff = i * ld + col0 + lane * 4;
+        auto issue = [&](int r) { async_issue_row<K, S>(A, ring, first, nr, col0, lane, r); };
+        if (!primed) {
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    if (col0 + kk * 128 + lane * 4 < n) {
-                        cp_async16(xs + kk * 128 + lane * 4, A.X + rowoff + kk * 128);
-                        cp_async16(cs_ + kk * 128 + lane * 4, A.C + rowoff + kk * 128);
-                    }
-                }
-            }
-            cp_async_commit();  // an empty group keeps the group count in step
-        };
-#pragma unroll
-        for (int r = 0; r < S - 1; ++r) issue(r);
+            for (int r = 0; r < S - 1; ++r) issue(r);
+        }
+        primed = false;
 
         float scx = 0.f, sd = 0.f;
         int since_flush = 0;
@@ -781,8 +819,8 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
     block_sum_f64<2, kThreads>(v, s_red);
     if (threadIdx.x == 0) {
         if (A.accumulate) {
-            atomicAdd(A.acc + 0, v[0]);
-            atomicAdd(A.acc + 1, v[1]);
+            atomicAdd(acc_at(A.acc, 0), v[0]);
+            atomicAdd(acc_at(A.acc, 1), v[1]);
         } else {
             A.ctapart[2 * blockIdx.x + 0] = v[0];
             A.ctapart[2 * blockIdx.x + 1] = v[1];
@@ -796,7 +834,7 @@ struct FinishArgs {
     const double* ctapart;
     double* u;              // accumulation mode: row totals, read and reset to 0
     double* v;              // accumulation mode: column totals, read and reset to 0
-    double* acc;            // accumulation mode: [8] <C,X>, sum [d]_+^2 and the six finish totals,
+    double* acc;            // accumulation mode: kAccSlots totals (acc_at): <C,X>, sum [d]_+^2, the six finish totals,
                             // read and reset by the last block
     int accumulate;
     const int* tile_slot;   // [T+1] first slot of each column tile
@@ -876,27 +914,50 @@ __device__ __forceinline__ bool arrive_last(Scalars* sc, int nblk) {
     return s_last != 0;
 }
 
-// Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1), executed by block
-// `blk` of the `nblk` blocks (of NT threads) that serve this problem.
+// Scalars the finish reads that the step before it does not write: the solve's
+// constants, and alpha, k and the last primal value, which only the previous finish
+// writes.  The single-problem finish kernel loads them before it waits for the step.
+struct FinishConsts {
+    double alpha, sum_p, sum_q, inv_rho, tol, primal;
+    long long k, max_iter;
+    int stop_rule;
+};
+
+__device__ __forceinline__ FinishConsts load_finish_consts(const Scalars* sc) {
+    FinishConsts K;
+    K.alpha = __ldcg(&sc->alpha);
+    K.sum_p = __ldcg(&sc->sum_p);
+    K.sum_q = __ldcg(&sc->sum_q);
+    K.inv_rho = __ldcg(&sc->inv_rho);
+    K.tol = __ldcg(&sc->tol);
+    K.primal = __ldcg(&sc->primal);
+    K.k = __ldcg(&sc->k);
+    K.max_iter = __ldcg(&sc->max_iter);
+    K.stop_rule = __ldcg(&sc->stop_rule);
+    return K;
+}
+
 // Scalar part of the finish (one thread): steps 5-8's scalars and the stopping test
-// from the totals tot[0..5] (sum r, ||r||_1 + ||s||_1, ||r||^2 + ||s||^2, p.g', q.h',
-// sum s), <C,X> and sum [phi + psi - rho C]_+^2.  Norms are kept squared on the device
-// (the host takes the square roots it reports), so the test needs no FP64 sqrt.
-__device__ __forceinline__ void finish_scalars(const FinishArgs& A, const double* tot, double scx, double sdx) {
+// (Sec. 3.1) from the totals tot[0..5] (sum r, ||r||_1 + ||s||_1, ||r||^2 + ||s||^2,
+// p.g', q.h', sum s), <C,X> and sum [phi + psi - rho C]_+^2.  Norms are kept squared on
+// the device (the host takes the square roots it reports), so the test needs no FP64
+// sqrt.  No fence before `done`: it is read by later kernels (after their wait for
+// this one or after a grid barrier, both of which order it) and by the host after the
+// stream's work has completed.
+__device__ __forceinline__ void finish_scalars(const FinishArgs& A, const double* tot, double scx, double sdx,
+                                               const FinishConsts& K) {
     Scalars* sc = A.sc;
-    const double alpha = __ldcg(&sc->alpha);
-    const double beta = tot[0] * A.inv_mn;            // step 5
-    const double c_new = 2.0 * beta - alpha;           // steps 6-7 scalar term
-    const double pphi = (tot[3] + c_new * sc->sum_p) * A.inv_n;
-    const double qpsi = (tot[4] + c_new * sc->sum_q) * A.inv_m;
-    const double inv_rho = sc->inv_rho;
-    const double primal = A.no_test ? __ldcg(&sc->primal) : scx;
-    const double dual = (pphi + qpsi) * inv_rho;
+    const double beta = tot[0] * A.inv_mn;             // step 5
+    const double c_new = 2.0 * beta - K.alpha;         // steps 6-7 scalar term
+    const double pphi = (tot[3] + c_new * K.sum_p) * A.inv_n;
+    const double qpsi = (tot[4] + c_new * K.sum_q) * A.inv_m;
+    const double primal = A.no_test ? K.primal : scx;
+    const double dual = (pphi + qpsi) * K.inv_rho;
     const double gap = fabs(primal - dual);
     const double res_l1 = tot[1];
     const double res_l2_sq = tot[2];
-    const double dres_sq = sdx * inv_rho * inv_rho;
-    sc->alpha = alpha - beta;                          // step 8
+    const double dres_sq = sdx * K.inv_rho * K.inv_rho;
+    sc->alpha = K.alpha - beta;                        // step 8
     sc->c = c_new;
     sc->beta = beta;
     if (!A.no_test) {
@@ -907,35 +968,54 @@ __device__ __forceinline__ void finish_scalars(const FinishArgs& A, const double
         sc->res_l2 = res_l2_sq;          // squared (see above)
         sc->dual_res_prev = dres_sq;     // squared
     }
-    const long long k = __ldcg(&sc->k) + 1;
+    const long long k = K.k + 1;
     sc->k = k;
     const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2_sq) &&
                         isfinite(dres_sq) && isfinite(c_new) && isfinite(tot[5]);
-    const int rule = sc->stop_rule;
-    const double tol = sc->tol;
+    const int rule = K.stop_rule;
+    const double tol = K.tol;
     const bool conv = !A.no_test && tol >= 0.0 && (!(rule & 1) || gap <= tol) && (!(rule & 2) || res_l1 <= tol) &&
                       (!(rule & 4) || dres_sq <= tol * tol);
     int done = kRunning;
     if (__ldcg(&sc->fault)) done = kFault;
     else if (!finite) done = kNonFinite;
     else if (conv) done = kConverged;
-    else if (k >= sc->max_iter) done = kIterCap;
+    else if (k >= K.max_iter) done = kIterCap;
     sc->counter = 0u;
-    __threadfence();
     sc->done = done;
+}
+
+// The first element of a finish thread, loaded before the wait for the step: p_i and
+// a_i (row) or q_j and b_j (column); the previous finish wrote a and b.
+struct FinishPre {
+    bool valid;
+    double pq, ab;
+};
+
+__device__ __forceinline__ FinishPre load_finish_pre(const FinishArgs& A, long long idx) {
+    FinishPre F{false, 0.0, 0.0};
+    if (idx < A.m) {
+        F = FinishPre{true, __ldcg(A.p + idx), __ldcg(A.a + idx)};
+    } else if (idx < A.m + A.n) {
+        F = FinishPre{true, __ldcg(A.q + idx - A.m), __ldcg(A.b + idx - A.m)};
+    }
+    return F;
 }
 
 // Steps 5-8 of Algorithm 1 and the stopping test (Sec. 3.1), executed by block
 // `blk` of the `nblk` blocks (of NT threads) that serve this problem.
 //
-// Accumulation mode: every warp reduces its six partial sums with shuffles and adds
-// them into FP64 totals (A.acc[2..7]) with atomics; the last block to arrive reads
-// the totals once.  Fixed-order mode: per-block partials (finpart) summed by the last
-// block in block order.  FP64 has a long dependent latency on this GPU, so the
-// accumulation path keeps the chain after the element work to one warp reduction,
-// one fence, one ticket and one read of the totals.
+// Accumulation mode: the block reduces its six partial sums (warp shuffles, then
+// shared memory) and thread 0 adds them into the FP64 totals with atomics and takes
+// a ticket; in the block that arrived last, thread 0 reads the totals once and
+// forms the scalars.  Fixed-order mode: per-block partials (finpart) summed by the
+// last block in block order.  FP64 has a long dependent latency on this GPU, so the
+// accumulation path keeps the chain after the element work to one block reduction,
+// one fence, one ticket and one read of the totals.  `pre` (optional) holds this
+// thread's first element and `kc` (optional) the scalars, both loaded earlier.
 template <int NT = kFinishThreads>
-__device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nblk) {
+__device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nblk, FinishPre pre = FinishPre{},
+                                            const FinishConsts* kc = nullptr) {
     __shared__ double s_red[NT / 32][kFinishAcc];
     Scalars* sc = A.sc;
 
@@ -945,27 +1025,30 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
     for (long long idx = (long long)blk * NT + threadIdx.x; idx < mn; idx += (long long)nblk * NT) {
         if (idx < A.m) {
             const long long i = idx;
-            const double r = row_total(A, i) - A.p[i];
-            const double ai = __ldcg(A.a + i);
+            const double pi = pre.valid ? pre.pq : A.p[i];
+            const double ai = pre.valid ? pre.ab : __ldcg(A.a + i);
+            const double r = row_total(A, i) - pi;
             const double gn = ai - 2.0 * r;
             A.a[i] = ai - r;
             A.g[i] = gn;
             acc[0] += r;
             acc[1] += fabs(r);
             acc[2] += r * r;
-            acc[3] += A.p[i] * gn;
+            acc[3] += pi * gn;
         } else {
             const long long j = idx - A.m;
-            const double s = col_total(A, j) - A.q[j];
-            const double bj = __ldcg(A.b + j);
+            const double qj = pre.valid ? pre.pq : A.q[j];
+            const double bj = pre.valid ? pre.ab : __ldcg(A.b + j);
+            const double s = col_total(A, j) - qj;
             const double hn = bj - 2.0 * s;
             A.b[j] = bj - s;
             A.h[j] = hn;
             acc[5] += s;
             acc[1] += fabs(s);
             acc[2] += s * s;
-            acc[4] += A.q[j] * hn;
+            acc[4] += qj * hn;
         }
+        pre.valid = false;
     }
     if (A.accumulate) {
 #pragma unroll
@@ -974,19 +1057,26 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
             for (int c = 0; c < kFinishAcc; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
         if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-            for (int c = 0; c < kFinishAcc; ++c) atomicAdd(A.acc + 2 + c, acc[c]);
-            __threadfence();
+            for (int c = 0; c < kFinishAcc; ++c) s_red[threadIdx.x >> 5][c] = acc[c];
         }
-        if (!arrive_last(sc, nblk)) return;
-        if (threadIdx.x == 0) {
-            double tot[kFinishAcc];
+        __syncthreads();
+        if (threadIdx.x != 0) return;
 #pragma unroll
-            for (int c = 0; c < kFinishAcc; ++c) tot[c] = __ldcg(A.acc + 2 + c);
-            const double scx = __ldcg(A.acc + 0), sdx = __ldcg(A.acc + 1);
+        for (int w = 1; w < NT / 32; ++w)
 #pragma unroll
-            for (int c = 0; c < kFinishAcc + 2; ++c) A.acc[c] = 0.0;
-            finish_scalars(A, tot, scx, sdx);
-        }
+            for (int c = 0; c < kFinishAcc; ++c) acc[c] += s_red[w][c];
+#pragma unroll
+        for (int c = 0; c < kFinishAcc; ++c) atomicAdd(acc_at(A.acc, 2 + c), acc[c]);
+        __threadfence();
+        if (atomicAdd(&sc->counter, 1u) != (unsigned int)nblk - 1u) return;
+        __threadfence();
+        double tot[kFinishAcc];
+#pragma unroll
+        for (int c = 0; c < kFinishAcc; ++c) tot[c] = __ldcg(acc_at(A.acc, 2 + c));
+        const double scx = __ldcg(acc_at(A.acc, 0)), sdx = __ldcg(acc_at(A.acc, 1));
+#pragma unroll
+        for (int c = 0; c < kAccSlots; ++c) *acc_at(A.acc, c) = 0.0;
+        finish_scalars(A, tot, scx, sdx, kc ? *kc : load_finish_consts(sc));
         return;
     }
 
@@ -1009,13 +1099,20 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
     }
     __shared__ double s_red2[NT / 32][kFinishAcc + 2];
     block_sum_f64<kFinishAcc + 2, NT>(tot, s_red2);
-    if (threadIdx.x == 0) finish_scalars(A, tot, tot[kFinishAcc + 0], tot[kFinishAcc + 1]);
+    if (threadIdx.x == 0)
+        finish_scalars(A, tot, tot[kFinishAcc + 0], tot[kFinishAcc + 1], kc ? *kc : load_finish_consts(sc));
 }
 
+// The finish of the single-problem graph.  It is launched as a programmatic dependent
+// of the step, so the loads that do not depend on the step (this thread's first
+// element of p, a / q, b and the scalars of FinishConsts) are issued before the wait.
 __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs A) {
+    const FinishPre pre = load_finish_pre(A, (long long)blockIdx.x * kFinishThreads + threadIdx.x);
+    const FinishConsts kc = load_finish_consts(A.sc);
     wait_for_predecessor();
+    release_dependents();  // the next step may start its blocks and its first copies of X and C
     if (A.sc->done != kRunning) return;
-    finish_body<kFinishThreads>(A, blockIdx.x, gridDim.x);
+    finish_body<kFinishThreads>(A, blockIdx.x, gridDim.x, pre, &kc);
 }
 
 // ------------------------------------------------------------------ persistent solve
