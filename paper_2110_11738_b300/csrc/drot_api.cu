@@ -675,8 +675,9 @@ drot_status autotune_shape(drot_handle *h, long long m, long long n, long long l
     cudaEvent_t e0, e1;
     DROT_CUDA(h, cudaEventCreate(&e0));
     DROT_CUDA(h, cudaEventCreate(&e1));
-    float best = 1e30f;
+    float best = 1e30f, dflt = 0.f;
     int best_v = 1, best_k = 1;
+    const int dflt_k = n >= 1536 ? 4 : (n >= 384 ? 2 : 1);  // make_plan's choice without tuning
     drot_status out = DROT_OK;
     for (int variant = 1; variant <= 3 && out == DROT_OK; ++variant) {
         for (int K : {1, 2, 4}) {
@@ -690,12 +691,13 @@ drot_status autotune_shape(drot_handle *h, long long m, long long n, long long l
             const drot::StepArgs A = step_args(h, P, m, n, ld, C, Xs);
             DROT_CUDA(h, launch_step<true>(P, A, h->stream));
             DROT_CUDA(h, cudaEventRecord(e0, h->stream));
-            for (int r = 0; r < 3; ++r) DROT_CUDA(h, launch_step<true>(P, A, h->stream));
+            for (int r = 0; r < 6; ++r) DROT_CUDA(h, launch_step<true>(P, A, h->stream));
             DROT_CUDA(h, cudaEventRecord(e1, h->stream));
             DROT_CUDA(h, cudaEventSynchronize(e1));
-            h->prof.kernel_launches += 4;
+            h->prof.kernel_launches += 7;
             float ms = 0.f;
             DROT_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (variant == 1 && K == dflt_k) dflt = ms;
             if (ms < best) {
                 best = ms;
                 best_v = variant;
@@ -706,6 +708,12 @@ drot_status autotune_shape(drot_handle *h, long long m, long long n, long long l
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != DROT_OK) return out;
+    // Keep the untuned choice unless a candidate beats it by 3 %: near-ties would
+    // otherwise flip between runs on timing noise.
+    if (dflt > 0.f && best > 0.97f * dflt) {
+        best_v = 1;
+        best_k = dflt_k;
+    }
     h->tuned.push_back({m, n, best_v, best_k});
     return DROT_OK;
 }
