@@ -108,6 +108,13 @@ typedef struct {
                                    and none of step_variant, tile_k, grid_ctas, persistent,
                                    deterministic, c_skip is set), 1 never, 2 required
                                    (DROT_ERR_INVALID_ARG if the problem does not fit; c_skip off) */
+    double *trace;              /* optional device buffer of 2 * trace_len doubles, written during a solve:
+                                   trace[2(k-1)] = <C, X_k> and trace[2(k-1)+1] = ||X_k 1 - p||_1 +
+                                   ||X_k^T 1 - q||_1 for iterations k = 1 .. min(K, trace_len) (the
+                                   quantities of the stopping test, Sec. 3.1; with c_skip only the
+                                   C-reading iterations are written).  NULL: no trace.  Setting it keeps
+                                   the automatic choice off the cluster-resident path, which has none */
+    int64_t trace_len;
 } drot_config;
 
 typedef struct {
@@ -139,7 +146,9 @@ typedef struct {
     int64_t kernel_launches;    /* all kernels this handle launched (including early exits) */
     int64_t graph_replays;      /* CUDA-graph replays issued */
     int32_t tile_k, grid_ctas, col_tiles, graph_iters;  /* the plan of the last solve */
-    int32_t step_variant, stages;                       /* fused-step variant and ring depth used */
+    int32_t step_variant, stages;                       /* fused-step variant (1 register-fed, 2 TMA-fed,
+                                                           3 async-copy ring, 4 cluster-resident, 5 FP64)
+                                                           and ring depth (cluster size for 4) used */
     double finish_ms_total;     /* summed device time of the finish launches of the timed iterations */
     double iter_ms_total;       /* summed device time from each timed step launch to the next one */
 } drot_profile;
@@ -168,6 +177,18 @@ drot_status drot_create(drot_handle **h, const drot_config *cfg);
 drot_status drot_solve(drot_handle *h, int64_t m, int64_t n, const float *C, int64_t ld,
                        const double *p, const double *q, double rho, double tol, int64_t max_iter,
                        float *X, double *mu, double *nu, int warm, drot_result *res);
+
+/* drot_solve in double precision (the paper runs its robustness experiments in FP32 and
+ * FP64, Sec. 4).  Same arguments and meaning as drot_solve, with C and X FP64: row pitch
+ * ld a multiple of 2 (16-byte aligned rows), 16-byte aligned base pointers.  Every
+ * quantity of Algorithm 1 is FP64 (entries, phi, psi, the per-entry update and all
+ * sums).  One step variant (register-fed, 256-column tiles, on the same work split,
+ * finish kernel and iteration graphs); step_variant, tile_k and autotune are ignored,
+ * the cluster-resident path is not used (cluster = 2: DROT_ERR_INVALID_ARG), and
+ * persistent or c_skip return DROT_ERR_INVALID_ARG. */
+drot_status drot_solve_f64(drot_handle *h, int64_t m, int64_t n, const double *C, int64_t ld,
+                           const double *p, const double *q, double rho, double tol, int64_t max_iter,
+                           double *X, double *mu, double *nu, int warm, drot_result *res);
 
 /* Solve B independent problems of uneven sizes (no counterpart in the paper, which
  * solves one problem at a time; each problem follows drot_solve exactly).  All problems

@@ -24,6 +24,7 @@
 #include "drot_batched.cuh"
 #include "drot_mlp.cuh"
 #include "drot_cluster.cuh"
+#include "drot_f64.cuh"
 
 using drot::Scalars;
 
@@ -42,11 +43,13 @@ struct GraphKey {
     long long m = -1, n = -1, ld = -1;
     const void *C = nullptr, *X = nullptr, *p = nullptr, *q = nullptr;
     const void *arena = nullptr;
-    int K = 0, G = 0, graph_iters = 0, profile = 0, variant = 0, accumulate = 0, c_skip = 0;
+    int K = 0, G = 0, graph_iters = 0, profile = 0, variant = 0, accumulate = 0, c_skip = 0, f64 = 0;
+    const void *trace = nullptr;
     bool operator==(const GraphKey &o) const {
         return m == o.m && n == o.n && ld == o.ld && C == o.C && X == o.X && p == o.p && q == o.q &&
                arena == o.arena && K == o.K && G == o.G && graph_iters == o.graph_iters && profile == o.profile &&
-               variant == o.variant && accumulate == o.accumulate && c_skip == o.c_skip;
+               variant == o.variant && accumulate == o.accumulate && c_skip == o.c_skip && f64 == o.f64 &&
+               trace == o.trace;
     }
 };
 
@@ -559,6 +562,8 @@ drot::FinishArgs finish_args(const drot_handle *h, long long m, long long n, con
     F.inv_n = 1.0 / (double)n;
     F.inv_m = 1.0 / (double)m;
     F.inv_mn = 1.0 / (double)(m + n);
+    F.trace = h->cfg.trace;
+    F.trace_len = h->cfg.trace ? h->cfg.trace_len : 0;
     return F;
 }
 
@@ -603,6 +608,12 @@ cudaError_t launch_step(const Plan &P, const drot::StepArgs &A, cudaStream_t s, 
     }
 }
 
+// The FP64 fused step (one variant; tiles of drot::kTileW64 columns, i.e. K = 2).
+template <bool UPDATE>
+cudaError_t launch_step64(const Plan &P, const drot::StepArgs64 &A, cudaStream_t s, bool pdl = false) {
+    return launch_k(drot::drot_step_f64_kernel<UPDATE>, dim3(P.G), dim3(drot::kThreads), 0, s, pdl, A);
+}
+
 void destroy_graphs(drot_handle *h) {
     for (int i = 0; i < 2; ++i) {
         if (h->exec[i]) cudaGraphExecDestroy(h->exec[i]);
@@ -615,7 +626,7 @@ void destroy_graphs(drot_handle *h) {
 
 // Capture `graph_iters` iterations of [step -> finish] into two executable graphs.
 drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, const drot::StepArgs &A,
-                         const drot::FinishArgs &F) {
+                         const drot::FinishArgs &F, const drot::StepArgs64 *A64 = nullptr) {
     destroy_graphs(h);
     const bool prof = key.profile != 0;
     for (int inst = 0; inst < 2; ++inst) {
@@ -633,8 +644,9 @@ drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, con
             if (prof) err = cudaEventRecordWithFlags(h->ev[inst][3 * it], h->stream, cudaEventRecordExternal);
             const bool pdl = !prof;  // an event record between kernels would break the programmatic edge
             if (err == cudaSuccess)
-                err = cskip ? launch_step_cskip(P, A, (it & 1) ? 2 : 1, h->stream, pdl)
-                            : launch_step<true>(P, A, h->stream, pdl);
+                err = A64     ? launch_step64<true>(P, *A64, h->stream, pdl)
+                      : cskip ? launch_step_cskip(P, A, (it & 1) ? 2 : 1, h->stream, pdl)
+                              : launch_step<true>(P, A, h->stream, pdl);
             if (prof && err == cudaSuccess)
                 err = cudaEventRecordWithFlags(h->ev[inst][3 * it + 1], h->stream, cudaEventRecordExternal);
             if (err == cudaSuccess) {
@@ -661,7 +673,8 @@ drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, con
 }
 
 // Time every fused-step plan candidate (variant x tile width) for this shape on a
-// scratch plan, three launches each after one warm-up, and keep the fastest.
+// scratch plan, six launches each after one warm-up, and keep the fastest (with a
+// 3 % margin in favour of the untuned plan).
 // Runs after the scalar state is uploaded (the kernels read rho and the done flag);
 // the real plan's set-up afterwards re-zeroes every total the candidates touched.
 drot_status autotune_shape(drot_handle *h, long long m, long long n, long long ld, const float *C) {
@@ -718,11 +731,15 @@ drot_status autotune_shape(drot_handle *h, long long m, long long n, long long l
     return DROT_OK;
 }
 
-// The solve on device pointers.
-drot_status solve_device(drot_handle *h, long long m, long long n, const float *C, long long ld, const double *p,
-                         const double *q, double rho, double tol, long long max_iter, float *X, double *mu,
-                         double *nu, int warm, drot_result *res) {
+// The solve on device pointers.  f64: C and X are FP64 (drot_solve_f64), else FP32.
+drot_status solve_device(drot_handle *h, long long m, long long n, const void *Cv, long long ld, const double *p,
+                         const double *q, double rho, double tol, long long max_iter, void *Xv, double *mu,
+                         double *nu, int warm, drot_result *res, bool f64 = false) {
     drot_status st = DROT_OK;
+    const float *C = f64 ? nullptr : static_cast<const float *>(Cv);
+    float *X = f64 ? nullptr : static_cast<float *>(Xv);
+    const double *C64 = f64 ? static_cast<const double *>(Cv) : nullptr;
+    double *X64 = f64 ? static_cast<double *>(Xv) : nullptr;
     // scalar state; marginal sums and the warm duals' sums first
     Scalars &S = *h->h_sc;
     std::memset(&S, 0, sizeof S);
@@ -746,26 +763,31 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     if (!(std::fabs(chk.sum_p - chk.sum_q) <= 1e-9 * std::max(1.0, std::fabs(chk.sum_p))))
         return fail(h, DROT_ERR_MARGINALS, "sum(p) = %.17g and sum(q) = %.17g differ", chk.sum_p, chk.sum_q);
 
-    if (h->cfg.autotune) {
+    if (f64 && (h->cfg.persistent || h->cfg.c_skip))
+        return fail(h, DROT_ERR_INVALID_ARG, "the FP64 solve has no persistent or C-skipping mode");
+    if (h->cfg.autotune && !f64) {
         st = autotune_shape(h, m, n, ld, C);
         if (st != DROT_OK) return st;
     }
     Plan P;
-    make_plan(h, m, n, P);
+    if (f64) make_plan(h, m, n, P, 1, drot::kTileW64 / 128);  // one FP64 variant, 256-column tiles
+    else make_plan(h, m, n, P);
     st = setup_workspace(h, m, n, P);
     if (st != DROT_OK) return st;
 
     // X_0 and the state derived from it
     if (!warm) {
-        const long long work = m * ((n + 3) / 4);
+        const long long work = f64 ? m * n : m * ((n + 3) / 4);
         const int blocks = (int)std::min<long long>(8LL * h->num_sms, std::max<long long>(1, (work + 255) / 256));
-        drot::drot_init_plan_kernel<<<blocks, 256, 0, h->stream>>>(X, p, q, m, n, ld);
+        if (f64) drot::drot_init_plan_f64_kernel<<<blocks, 256, 0, h->stream>>>(X64, p, q, m, n, ld);
+        else drot::drot_init_plan_kernel<<<blocks, 256, 0, h->stream>>>(X, p, q, m, n, ld);
         DROT_CUDA(h, cudaGetLastError());
         h->prof.kernel_launches += 1;
     }
     const drot::StepArgs A = step_args(h, P, m, n, ld, C, X);
     const drot::FinishArgs F = finish_args(h, m, n, P, p, q);
-    DROT_CUDA(h, launch_step<false>(P, A, h->stream));
+    const drot::StepArgs64 A64{A, C64, X64};
+    DROT_CUDA(h, f64 ? launch_step64<false>(P, A64, h->stream) : launch_step<false>(P, A, h->stream));
     drot::drot_init_state_kernel<<<P.fin_blocks, drot::kFinishThreads, 0, h->stream>>>(F, warm ? mu : nullptr,
                                                                                       warm ? nu : nullptr);
     DROT_CUDA(h, cudaGetLastError());
@@ -776,9 +798,11 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     const ClusterPlan cp = cluster_plan(m, n);
     // automatic: only when no setting asks for the streaming path explicitly
     const bool explicit_stream = h->cfg.step_variant != 0 || h->cfg.tile_k != 0 || h->cfg.grid_ctas != 0 ||
-                                 h->cfg.persistent || h->cfg.deterministic || h->cfg.c_skip;
-    const bool use_cluster = cp.cs > 0 && !h->cfg.c_skip &&
+                                 h->cfg.persistent || h->cfg.deterministic || h->cfg.c_skip || h->cfg.trace;
+    const bool use_cluster = cp.cs > 0 && !h->cfg.c_skip && !f64 &&
                              (h->cfg.cluster == 2 || (h->cfg.cluster == 0 && !explicit_stream));
+    if (h->cfg.cluster == 2 && f64)
+        return fail(h, DROT_ERR_INVALID_ARG, "the cluster-resident solve is FP32 only");
     if (h->cfg.cluster == 2 && !use_cluster)
         return fail(h, DROT_ERR_INVALID_ARG, "a %lld x %lld problem does not fit on one cluster", m, n);
     if (max_iter > 0 && use_cluster) {
@@ -846,14 +870,16 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
             return fail(h, DROT_ERR_CUDA, "persistent iteration did not report completion");
     } else if (max_iter > 0) {
         GraphKey key;
-        key.m = m; key.n = n; key.ld = ld; key.C = C; key.X = X; key.p = p; key.q = q;
+        key.m = m; key.n = n; key.ld = ld; key.C = Cv; key.X = Xv; key.p = p; key.q = q;
+        key.f64 = f64 ? 1 : 0;
+        key.trace = h->cfg.trace;
         key.arena = h->work.ptr; key.K = P.K; key.G = P.G; key.graph_iters = P.graph_iters;
         key.variant = P.variant;
         key.accumulate = P.accumulate;
         key.c_skip = h->cfg.c_skip ? 1 : 0;
         key.profile = h->cfg.profile ? 1 : 0;
         if (!(key == h->key) || !h->exec[0]) {
-            st = build_graphs(h, key, P, A, F);
+            st = build_graphs(h, key, P, A, F, f64 ? &A64 : nullptr);
             if (st != DROT_OK) return st;
         }
         // keep two replays in flight; slot r%2 of h_status receives replay r's state
@@ -938,7 +964,8 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     DROT_CUDA(h, cudaGetLastError());
     DROT_CUDA(h, cudaMemsetAsync(&h->d_sc->nnz, 0, sizeof(unsigned long long), h->stream));
     const int nblocks = (int)std::min<long long>(8LL * h->num_sms, std::max<long long>(1, (m * n + 255) / 256));
-    drot::drot_count_nnz_kernel<<<nblocks, 256, 0, h->stream>>>(X, m, n, ld, h->d_sc);
+    if (f64) drot::drot_count_nnz_f64_kernel<<<nblocks, 256, 0, h->stream>>>(X64, m, n, ld, h->d_sc);
+    else drot::drot_count_nnz_kernel<<<nblocks, 256, 0, h->stream>>>(X, m, n, ld, h->d_sc);
     DROT_CUDA(h, cudaGetLastError());
     h->prof.kernel_launches += 2;
     DROT_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
@@ -950,7 +977,7 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const float *
     h->prof.grid_ctas = P.G;
     h->prof.col_tiles = P.T;
     h->prof.graph_iters = P.graph_iters;
-    h->prof.step_variant = use_cluster && max_iter > 0 ? 4 : P.variant;
+    h->prof.step_variant = f64 ? 5 : (use_cluster && max_iter > 0 ? 4 : P.variant);
     h->prof.stages = use_cluster && max_iter > 0 ? cp.cs : P.S;
 
     drot_status out = DROT_OK;
@@ -1314,11 +1341,14 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     return first_bad;
 }
 
-drot_status check_args(drot_handle *h, long long m, long long n, const float *C, long long ld, const double *p,
-                       const double *q, double tol, long long max_iter, float *X, double *mu, double *nu) {
+drot_status check_args(drot_handle *h, long long m, long long n, const void *C, long long ld, const double *p,
+                       const double *q, double tol, long long max_iter, void *X, double *mu, double *nu,
+                       size_t elem = sizeof(float)) {
     if (!h) return DROT_ERR_INVALID_ARG;
     if (m < 1 || n < 1) return fail(h, DROT_ERR_INVALID_ARG, "m = %lld and n = %lld must be >= 1", m, n);
-    if (ld < n || ld % 4 != 0) return fail(h, DROT_ERR_INVALID_ARG, "ld = %lld must be >= n and a multiple of 4", ld);
+    const long long vec = 16 / (long long)elem;  // rows start on 16-byte boundaries
+    if (ld < n || ld % vec != 0)
+        return fail(h, DROT_ERR_INVALID_ARG, "ld = %lld must be >= n and a multiple of %lld", ld, vec);
     if (!C || !p || !q || !X || !mu || !nu) return fail(h, DROT_ERR_INVALID_ARG, "a buffer pointer is NULL");
     if ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15)
         return fail(h, DROT_ERR_INVALID_ARG, "C and X must be 16-byte aligned");
@@ -1329,6 +1359,61 @@ drot_status check_args(drot_handle *h, long long m, long long n, const float *C,
     if (std::isnan(tol)) return fail(h, DROT_ERR_INVALID_ARG, "tol is NaN");
     if (m > (1LL << 40) / n) return fail(h, DROT_ERR_INVALID_ARG, "m * n too large");
     return DROT_OK;
+}
+
+// drot_solve (T = float) and drot_solve_f64 (T = double): argument checks, then the
+// device solve, directly on device buffers or through a staging workspace for host buffers.
+template <typename T>
+drot_status solve_entry(drot_handle *h, int64_t m, int64_t n, const T *C, int64_t ld, const double *p,
+                        const double *q, double rho, double tol, int64_t max_iter, T *X, double *mu, double *nu,
+                        int warm, drot_result *res) {
+    constexpr bool f64 = sizeof(T) == sizeof(double);
+    const auto t0 = std::chrono::steady_clock::now();
+    drot_status st = check_args(h, m, n, C, ld, p, q, tol, max_iter, X, mu, nu, sizeof(T));
+    if (st != DROT_OK) return st;
+    h->last_error.clear();
+    if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, DROT_ERR_CUDA, "cudaSetDevice failed");
+    if (!(rho > 0.0)) rho = h->cfg.rho0 / (double)(m + n);
+    if (!std::isfinite(rho)) return fail(h, DROT_ERR_INVALID_ARG, "rho is not finite");
+
+    const void *ptrs[7] = {C, p, q, X, mu, nu, nullptr};
+    int ndev = 0;
+    for (int i = 0; i < 6; ++i) ndev += is_device_ptr(ptrs[i], h->device) ? 1 : 0;
+    if (ndev != 0 && ndev != 6)
+        return fail(h, DROT_ERR_INVALID_ARG, "buffers mix device and host memory (%d of 6 on the device)", ndev);
+
+    if (ndev == 6) {
+        st = solve_device(h, m, n, C, ld, p, q, rho, tol, max_iter, X, mu, nu, warm, res, f64);
+    } else {
+        // host buffers: stage through a device workspace owned by the handle
+        const size_t mat = align_up(sizeof(T) * (size_t)m * ld, 256);
+        const size_t vm = align_up(sizeof(double) * m, 256), vn = align_up(sizeof(double) * n, 256);
+        st = arena_reserve(h, h->staging, 2 * mat + 2 * vm + 2 * vn);
+        if (st != DROT_OK) return st;
+        char *cur = static_cast<char *>(h->staging.ptr);
+        T *dC = carve<T>(cur, (size_t)m * ld);
+        T *dX = carve<T>(cur, (size_t)m * ld);
+        double *dp = carve<double>(cur, m), *dmu = carve<double>(cur, m);
+        double *dq = carve<double>(cur, n), *dnu = carve<double>(cur, n);
+        const size_t mb = sizeof(T) * (size_t)m * ld;
+        DROT_CUDA(h, cudaMemcpyAsync(dC, C, mb, cudaMemcpyHostToDevice, h->stream));
+        DROT_CUDA(h, cudaMemcpyAsync(dp, p, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+        DROT_CUDA(h, cudaMemcpyAsync(dq, q, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        if (warm) {
+            DROT_CUDA(h, cudaMemcpyAsync(dX, X, mb, cudaMemcpyHostToDevice, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(dmu, mu, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(dnu, nu, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        }
+        st = solve_device(h, m, n, dC, ld, dp, dq, rho, tol, max_iter, dX, dmu, dnu, warm, res, f64);
+        if (st == DROT_OK || st == DROT_NOT_CONVERGED || st == DROT_ERR_NONFINITE) {
+            DROT_CUDA(h, cudaMemcpyAsync(X, dX, mb, cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(mu, dmu, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaMemcpyAsync(nu, dnu, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+        }
+    }
+    if (res) res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
 }
 
 }  // namespace
@@ -1414,52 +1499,13 @@ drot_status drot_destroy(drot_handle *h) {
 drot_status drot_solve(drot_handle *h, int64_t m, int64_t n, const float *C, int64_t ld, const double *p,
                        const double *q, double rho, double tol, int64_t max_iter, float *X, double *mu, double *nu,
                        int warm, drot_result *res) {
-    const auto t0 = std::chrono::steady_clock::now();
-    drot_status st = check_args(h, m, n, C, ld, p, q, tol, max_iter, X, mu, nu);
-    if (st != DROT_OK) return st;
-    h->last_error.clear();
-    if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, DROT_ERR_CUDA, "cudaSetDevice failed");
-    if (!(rho > 0.0)) rho = h->cfg.rho0 / (double)(m + n);
-    if (!std::isfinite(rho)) return fail(h, DROT_ERR_INVALID_ARG, "rho is not finite");
+    return solve_entry<float>(h, m, n, C, ld, p, q, rho, tol, max_iter, X, mu, nu, warm, res);
+}
 
-    const void *ptrs[7] = {C, p, q, X, mu, nu, nullptr};
-    int ndev = 0;
-    for (int i = 0; i < 6; ++i) ndev += is_device_ptr(ptrs[i], h->device) ? 1 : 0;
-    if (ndev != 0 && ndev != 6)
-        return fail(h, DROT_ERR_INVALID_ARG, "buffers mix device and host memory (%d of 6 on the device)", ndev);
-
-    if (ndev == 6) {
-        st = solve_device(h, m, n, C, ld, p, q, rho, tol, max_iter, X, mu, nu, warm, res);
-    } else {
-        // host buffers: stage through a device workspace owned by the handle
-        const size_t mat = align_up(sizeof(float) * (size_t)m * ld, 256);
-        const size_t vm = align_up(sizeof(double) * m, 256), vn = align_up(sizeof(double) * n, 256);
-        st = arena_reserve(h, h->staging, 2 * mat + 2 * vm + 2 * vn);
-        if (st != DROT_OK) return st;
-        char *cur = static_cast<char *>(h->staging.ptr);
-        float *dC = carve<float>(cur, (size_t)m * ld);
-        float *dX = carve<float>(cur, (size_t)m * ld);
-        double *dp = carve<double>(cur, m), *dmu = carve<double>(cur, m);
-        double *dq = carve<double>(cur, n), *dnu = carve<double>(cur, n);
-        const size_t mb = sizeof(float) * (size_t)m * ld;
-        DROT_CUDA(h, cudaMemcpyAsync(dC, C, mb, cudaMemcpyHostToDevice, h->stream));
-        DROT_CUDA(h, cudaMemcpyAsync(dp, p, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
-        DROT_CUDA(h, cudaMemcpyAsync(dq, q, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-        if (warm) {
-            DROT_CUDA(h, cudaMemcpyAsync(dX, X, mb, cudaMemcpyHostToDevice, h->stream));
-            DROT_CUDA(h, cudaMemcpyAsync(dmu, mu, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
-            DROT_CUDA(h, cudaMemcpyAsync(dnu, nu, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-        }
-        st = solve_device(h, m, n, dC, ld, dp, dq, rho, tol, max_iter, dX, dmu, dnu, warm, res);
-        if (st == DROT_OK || st == DROT_NOT_CONVERGED || st == DROT_ERR_NONFINITE) {
-            DROT_CUDA(h, cudaMemcpyAsync(X, dX, mb, cudaMemcpyDeviceToHost, h->stream));
-            DROT_CUDA(h, cudaMemcpyAsync(mu, dmu, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
-            DROT_CUDA(h, cudaMemcpyAsync(nu, dnu, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
-            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
-        }
-    }
-    if (res) res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return st;
+drot_status drot_solve_f64(drot_handle *h, int64_t m, int64_t n, const double *C, int64_t ld, const double *p,
+                           const double *q, double rho, double tol, int64_t max_iter, double *X, double *mu,
+                           double *nu, int warm, drot_result *res) {
+    return solve_entry<double>(h, m, n, C, ld, p, q, rho, tol, max_iter, X, mu, nu, warm, res);
 }
 
 drot_status drot_solve_batched(drot_handle *h, int32_t B, const drot_problem *probs, double tol, int64_t max_iter,

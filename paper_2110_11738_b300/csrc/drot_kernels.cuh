@@ -851,6 +851,8 @@ struct FinishArgs {
     double inv_n, inv_m;
     double inv_mn;          // 1 / (m + n)
     int no_test;            // 1: the preceding pass had no C (C-skipping): <C,X> unknown, no stopping test
+    double* trace;          // optional: [2 * trace_len] <C, X_k> and ||r||_1 + ||s||_1 of iterate k at 2(k-1)
+    long long trace_len;
 };
 
 // Sum of `count` partials spaced `stride` apart, in a fixed order: four
@@ -970,6 +972,10 @@ __device__ __forceinline__ void finish_scalars(const FinishArgs& A, const double
     }
     const long long k = K.k + 1;
     sc->k = k;
+    if (A.trace && !A.no_test && k <= A.trace_len) {
+        A.trace[2 * (k - 1)] = primal;
+        A.trace[2 * (k - 1) + 1] = res_l1;
+    }
     const bool finite = isfinite(primal) && isfinite(dual) && isfinite(res_l1) && isfinite(res_l2_sq) &&
                         isfinite(dres_sq) && isfinite(c_new) && isfinite(tot[5]);
     const int rule = K.stop_rule;

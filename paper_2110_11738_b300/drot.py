@@ -38,7 +38,7 @@ STATUS_NAMES = {
 }
 
 # Every symbol include/drot.h declares.
-EXPORTED = ("drot_config_default", "drot_create", "drot_solve", "drot_solve_batched", "drot_destroy",
+EXPORTED = ("drot_config_default", "drot_create", "drot_solve", "drot_solve_f64", "drot_solve_batched", "drot_destroy",
             "drot_get_profile", "drot_reset_profile", "drot_status_string", "drot_last_error",
             "drot_solve_static", "drot_mlp_create", "drot_mlp_destroy", "drot_mlp_set_params",
             "drot_mlp_get_params", "drot_mlp_features", "drot_mlp_forward", "drot_mlp_train_step",
@@ -54,7 +54,8 @@ class DrotConfig(ctypes.Structure):
                 ("rho0", ctypes.c_double), ("graph_iters", ctypes.c_int), ("tile_k", ctypes.c_int),
                 ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int), ("step_variant", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("c_skip", ctypes.c_int), ("cluster", ctypes.c_int)]
+                ("c_skip", ctypes.c_int), ("cluster", ctypes.c_int), ("trace", ctypes.c_void_p),
+                ("trace_len", ctypes.c_int64)]
 
 
 class DrotResult(ctypes.Structure):
@@ -113,6 +114,8 @@ def load(build_if_missing: bool = True):
     lib.drot_solve.restype = ctypes.c_int
     lib.drot_solve.argtypes = [vp, i64, i64, vp, i64, vp, vp, ctypes.c_double, ctypes.c_double, i64, vp, vp, vp,
                                ctypes.c_int, ctypes.POINTER(DrotResult)]
+    lib.drot_solve_f64.restype = ctypes.c_int
+    lib.drot_solve_f64.argtypes = list(lib.drot_solve.argtypes)
     lib.drot_solve_batched.restype = ctypes.c_int
     lib.drot_solve_batched.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(DrotProblem), ctypes.c_double, i64,
                                        ctypes.c_int, ctypes.POINTER(DrotResult)]
@@ -166,8 +169,10 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
                 rho0: float = 2.0, graph_iters: int = 0, tile_k: int = 0, grid_ctas: int = 0,
                 profile: bool = False, step_variant: int = 0, deterministic: bool = False,
                 autotune: bool = False, persistent: bool = False, c_skip: bool = False,
-                cluster: int = 0) -> int:
-    """Create a solver handle; returns the opaque handle as an int."""
+                cluster: int = 0, trace=None) -> int:
+    """Create a solver handle; returns the opaque handle as an int.  ``trace``: optional float64
+    CUDA tensor of 2 * L entries that receives <C, X_k> and the l1 residual of iterations 1 .. L
+    of every solve (the caller keeps it alive while the handle is used)."""
     lib = load()
     cfg = DrotConfig()
     lib.drot_config_default(ctypes.byref(cfg))
@@ -185,6 +190,9 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
     cfg.persistent = int(bool(persistent))
     cfg.c_skip = int(bool(c_skip))
     cfg.cluster = int(cluster)
+    if trace is not None:
+        cfg.trace = _ptr(trace)
+        cfg.trace_len = int(trace.numel()) // 2
     h = ctypes.c_void_p()
     st = lib.drot_create(ctypes.byref(h), ctypes.byref(cfg))
     if st != DROT_OK:
@@ -204,6 +212,10 @@ def _ptr(x) -> int:
     return x.data_ptr()
 
 
+def _is_f64(x) -> bool:
+    return str(x.dtype) in ("float64", "torch.float64")
+
+
 def _ld_of(C) -> int:
     if isinstance(C, np.ndarray):
         return C.strides[0] // C.itemsize
@@ -217,7 +229,7 @@ def drot_solve(handle: int, C, p, q, rho: float = 0.0, tol: float = 1e-6, max_it
 
     C and X: float32, shape (m, ld) or a row-strided (m, n) view, unit column
     stride; p, q, mu, nu: float64.  X, mu, nu are written in place.  ``n``
-    defaults to C.shape[1].
+    defaults to C.shape[1].  float64 C and X call drot_solve_f64 instead.
     """
     lib = load()
     m = int(C.shape[0]) if m is None else int(m)
@@ -226,7 +238,10 @@ def drot_solve(handle: int, C, p, q, rho: float = 0.0, tol: float = 1e-6, max_it
     if X is not None and _ld_of(X) != ld:
         raise ValueError("C and X must share the row pitch")
     res = DrotResult()
-    st = lib.drot_solve(ctypes.c_void_p(handle), m, n, ctypes.c_void_p(_ptr(C)), ld, ctypes.c_void_p(_ptr(p)),
+    entry = lib.drot_solve_f64 if _is_f64(C) else lib.drot_solve
+    if X is not None and _is_f64(X) != _is_f64(C):
+        raise ValueError("C and X must have the same dtype")
+    st = entry(ctypes.c_void_p(handle), m, n, ctypes.c_void_p(_ptr(C)), ld, ctypes.c_void_p(_ptr(p)),
                         ctypes.c_void_p(_ptr(q)), float(rho), float(tol), int(max_iter),
                         ctypes.c_void_p(_ptr(X)), ctypes.c_void_p(_ptr(mu)), ctypes.c_void_p(_ptr(nu)),
                         int(bool(warm)), ctypes.byref(res))
@@ -313,6 +328,7 @@ class Solver:
         if not torch.cuda.is_available():
             raise RuntimeError("the DROT solver needs a CUDA device")
         self.device = int(device)
+        self._trace = cfg.get("trace")  # the handle writes into it: keep it alive
         self.handle = drot_create(device=self.device, **cfg)
 
     def close(self):
@@ -343,7 +359,7 @@ class Solver:
         n = int(C.shape[1]) if n is None else int(n)
         if X is None:
             ld = _ld_of(C)
-            X = torch.empty((m, ld), dtype=torch.float32, device=dev)[:, :n]
+            X = torch.empty((m, ld), dtype=C.dtype, device=dev)[:, :n]
         if mu is None:
             mu = torch.zeros(m, dtype=torch.float64, device=dev)
         if nu is None:
@@ -368,15 +384,17 @@ class Solver:
         drot_reset_profile(self.handle)
 
 
-def padded_matrix(A, ld: Optional[int] = None, device=None):
-    """Copy a (m, n) float32 matrix into a (m, ld) tensor with 16-byte aligned rows; returns the
-    (m, n) view (row stride ld) that drot_solve accepts."""
+def padded_matrix(A, ld: Optional[int] = None, device=None, dtype=None):
+    """Copy a (m, n) matrix into a (m, ld) float32 (or ``dtype``) tensor with 16-byte aligned rows;
+    returns the (m, n) view (row stride ld) that drot_solve (drot_solve_f64 for float64) accepts."""
     import torch
 
-    A = torch.as_tensor(A, dtype=torch.float32)
+    dtype = torch.float32 if dtype is None else dtype
+    A = torch.as_tensor(A, dtype=dtype)
     m, n = A.shape
-    ld = (n + 3) // 4 * 4 if ld is None else int(ld)
-    buf = torch.zeros((m, ld), dtype=torch.float32, device=device if device is not None else A.device)
+    vec = 16 // A.element_size()
+    ld = (n + vec - 1) // vec * vec if ld is None else int(ld)
+    buf = torch.zeros((m, ld), dtype=dtype, device=device if device is not None else A.device)
     buf[:, :n] = A.to(buf.device)
     return buf[:, :n]
 

@@ -18,7 +18,7 @@ HEADER = os.path.join(ROOT, "include", "drot.h")
 def _declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(drot_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(drot_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_library_builds_and_exports_every_declared_symbol():
@@ -30,7 +30,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     for name in declared:
         assert hasattr(lib, name), name
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r" T (drot_[a-z_]+)$", out, flags=re.M))
+    exported = set(re.findall(r" T (drot_[a-z0-9_]+)$", out, flags=re.M))
     assert set(declared) <= exported
 
 
