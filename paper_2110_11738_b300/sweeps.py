@@ -1,0 +1,267 @@
+"""Paper-shaped sweeps (Sec. 4) on the B300 solver.
+
+* ``e1``  robustness profile: for m = n = 512 and 100 random problems of the paper's
+  generator (2-D Gaussians with random means and covariances, target means around 5
+  with spread sigma_t, C = squared distances scaled to max 1, uniform marginals),
+  rho = 2 / (m + n), stop when the constraint violation ||X1 - p||_1 + ||X^T 1 - q||_1
+  falls below 1e-4 or after 1000 iterations; report the fraction of problems whose
+  relative objective error |f(X_K) - f*| / f* is at most eps, for eps on a grid, in
+  FP32 (drot_solve) and FP64 (drot_solve_f64).
+* ``e3``  time to accuracy: m = n from 100 to 20000, rho = 1 / (ln(m) (m + n)), X_0 = p q^T;
+  the time until the total error |f(X_k) - f*| / f* + ||X_k 1 - p||_1 + ||X_k^T 1 - q||_1
+  first reaches eps, for several eps.
+* ``runtime``  median per-iteration time (and 95 % interval) against m = n, each run the
+  difference of a 200- and a 100-iteration solve divided by 100 (set-up cancels).
+
+f* is exact where it can be: with uniform marginals and m = n the transport polytope's
+vertices are permutation matrices scaled by 1/n (Birkhoff-von Neumann), so f* is the
+optimal assignment cost / n (SciPy's linear_sum_assignment), used up to m = 2000.  Above
+that, f* is the primal value of an FP32 drot_solve (rho = 2 / (m + n)) stopped at gap <= 1e-7
+or after 100000 iterations (the gap reached is recorded); its error is negligible at eps >= 1e-3.
+
+Usage: python -m paper_2110_11738_b300.sweeps {e1,e3,runtime} [options] [--out results.json]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import statistics
+import sys
+import time
+from typing import Optional, Sequence
+
+import numpy as np
+
+EPS_GRID = tuple(10.0 ** e for e in np.arange(-6.0, -0.99, 0.25))
+
+
+def success_profile(rel_err: Sequence[float], eps_grid: Sequence[float] = EPS_GRID) -> list:
+    """Fraction of problems with relative error <= eps, for each eps of the grid
+    (a NaN or infinite error counts as a failure)."""
+    e = np.asarray(rel_err, dtype=np.float64)
+    ok = np.isfinite(e)
+    return [float(np.mean(ok & (e <= t))) if e.size else 0.0 for t in eps_grid]
+
+
+def first_below(err: Sequence[float], eps: float) -> Optional[int]:
+    """1-based index of the first entry <= eps (None if there is none)."""
+    idx = np.nonzero(np.asarray(err) <= eps)[0]
+    return int(idx[0]) + 1 if idx.size else None
+
+
+def cost64(pr) -> np.ndarray:
+    d = pr.x[:, None, :] - pr.y[None, :, :]
+    return (d * d).sum(-1) / pr.cost_scale
+
+
+def assignment_optimum(C: np.ndarray) -> float:
+    """Optimal transport cost for uniform marginals and m = n: min over permutations of
+    (1/n) sum_i C[i, sigma(i)]."""
+    from scipy.optimize import linear_sum_assignment
+
+    r, c = linear_sum_assignment(C)
+    return float(C[r, c].sum() / C.shape[0])
+
+
+def _device_problem(pr, f64: bool, device: int = 0):
+    import torch
+
+    from . import drot
+
+    dtype = torch.float64 if f64 else torch.float32
+    dev = torch.device("cuda", device)
+    C = drot.padded_matrix(cost64(pr) if f64 else pr.C, device=dev, dtype=dtype)
+    X = torch.zeros((pr.m, C.stride(0)), dtype=dtype, device=dev)[:, : pr.n]
+    p = torch.as_tensor(pr.p, dtype=torch.float64, device=dev)
+    q = torch.as_tensor(pr.q, dtype=torch.float64, device=dev)
+    mu = torch.zeros(pr.m, dtype=torch.float64, device=dev)
+    nu = torch.zeros(pr.n, dtype=torch.float64, device=dev)
+    return C, p, q, X, mu, nu
+
+
+def _paper_problem(m: int, seed: int, sigma_t: float):
+    import workloads
+
+    return workloads.make_problem("paper_gauss", seed=seed, m=m, n=m, sigma_t=sigma_t)
+
+
+def _solve(solver, args, **kw):
+    C, p, q, X, mu, nu = args
+    return solver.solve(C, p, q, X=X, mu=mu, nu=nu, **kw)
+
+
+def _timed_solve(solver, args, **kw):
+    """One solve timed with CUDA events on the current stream (the solver synchronises it)."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = _solve(solver, args, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) * 1e-3
+
+
+# ---------------------------------------------------------------- E1
+
+def robustness(problems: int = 100, m: int = 512, sigma_t: float = 5.0, f64: bool = False, rho0: float = 2.0,
+               viol_tol: float = 1e-4, max_iter: int = 1000, seed0: int = 0, device: int = 0) -> dict:
+    from . import drot
+
+    rel, iters, status = [], [], []
+    with drot.Solver(device=device, stop_rule=drot.STOP_RES_L1) as s:
+        for k in range(problems):
+            pr = _paper_problem(m, seed0 + k, sigma_t)
+            fstar = assignment_optimum(cost64(pr))
+            rho = rho0 / (2.0 * m)
+            out = _solve(s, _device_problem(pr, f64, device), rho=rho, tol=viol_tol, max_iter=max_iter, check=False)
+            rel.append(abs(out["primal_obj"] - fstar) / fstar)
+            iters.append(out["iters"])
+            status.append(out["status_name"])
+    return dict(experiment="e1", m=m, n=m, problems=problems, sigma_t=sigma_t, precision="f64" if f64 else "f32",
+                rho0=rho0, viol_tol=viol_tol, max_iter=max_iter, seed0=seed0, rel_err=rel, iters=iters,
+                status=status, eps_grid=list(EPS_GRID), profile=success_profile(rel))
+
+
+# ---------------------------------------------------------------- E3
+
+def time_to_accuracy(sizes: Sequence[int] = (100, 512, 2000, 5000, 10000, 20000),
+                     eps_list: Sequence[float] = (1e-1, 1e-2, 1e-3), runs: int = 3, sigma_t: float = 5.0,
+                     k_start: int = 1000, k_cap: int = 400_000, exact_upto: int = 2000, ref_gap: float = 1e-7,
+                     ref_iters: int = 100_000, device: int = 0) -> dict:
+    import torch
+
+    from . import drot
+
+    rows = []
+    for m in sizes:
+        for r in range(runs):
+            pr = _paper_problem(m, 7919 * m + r, sigma_t)
+            rho = 1.0 / (math.log(m) * 2.0 * m)
+            if m <= exact_upto:
+                fstar, fsrc = assignment_optimum(cost64(pr)), "assignment"
+            else:
+                # stop on the gap alone: the l1 residual of FP32 iterates has a rounding floor that
+                # grows with m + n (about 1e-5 at m = n = 20000) and would never reach the tolerance
+                with drot.Solver(device=device, stop_rule=drot.STOP_GAP) as s:
+                    ref = _solve(s, _device_problem(pr, False, device), tol=ref_gap, max_iter=ref_iters, check=False)
+                fstar = ref["primal_obj"]
+                fsrc = f"drot {ref['iters']} iterations, gap {ref['gap']:.1e}, l1 residual {ref['res_l1']:.1e}"
+            # iterations to each eps from the device trace (the run grows until the smallest eps is met)
+            k, err = k_start, None
+            while True:
+                trace = torch.full((2 * k,), np.nan, dtype=torch.float64, device=f"cuda:{device}")
+                with drot.Solver(device=device, trace=trace) as s:
+                    _solve(s, _device_problem(pr, False, device), rho=rho, tol=-1.0, max_iter=k)
+                tr = trace.cpu().numpy().reshape(-1, 2)
+                err = np.abs(tr[:, 0] - fstar) / fstar + tr[:, 1]
+                if first_below(err, min(eps_list)) is not None or k >= k_cap:
+                    break
+                k = min(4 * k, k_cap)
+            row = dict(m=m, run=r, fstar=fstar, fstar_source=fsrc, rho=rho, iters={}, seconds={})
+            with drot.Solver(device=device) as s:
+                # the same buffers for every timed solve (each restarts from X_0 = p q^T), so the
+                # plan and the iteration graphs are built once, in the untimed first solve
+                args = _device_problem(pr, False, device)
+                _timed_solve(s, args, rho=rho, tol=-1.0, max_iter=10)
+                for eps in eps_list:
+                    ke = first_below(err, eps)
+                    row["iters"][str(eps)] = ke
+                    if ke is None:
+                        row["seconds"][str(eps)] = None
+                        continue
+                    _, secs = _timed_solve(s, args, rho=rho, tol=-1.0, max_iter=ke)
+                    row["seconds"][str(eps)] = secs
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    summary = {}
+    for m in sizes:
+        for eps in eps_list:
+            t = [rw["seconds"][str(eps)] for rw in rows if rw["m"] == m]
+            k = [rw["iters"][str(eps)] for rw in rows if rw["m"] == m]
+            done = [x for x in t if x is not None]
+            summary[f"{m}/{eps}"] = dict(median_seconds=statistics.median(done) if done else None,
+                                        median_iters=statistics.median([x for x in k if x is not None])
+                                        if done else None, reached=len(done), runs=len(t))
+    return dict(experiment="e3", sizes=list(sizes), eps=list(eps_list), runs=runs, sigma_t=sigma_t, rows=rows,
+                summary=summary)
+
+
+# ---------------------------------------------------------------- runtime per iteration
+
+def runtime_per_iteration(sizes: Sequence[int] = (100, 200, 500, 1000, 2000, 5000, 10000, 20000), runs: int = 10,
+                          iters: int = 100, sigma_t: float = 5.0, device: int = 0, **cfg) -> dict:
+    """``cfg``: solver configuration (drot_create keywords), e.g. persistent=True."""
+    from . import drot
+
+    rows = []
+    for m in sizes:
+        pr = _paper_problem(m, 31 * m, sigma_t)
+        rho = 2.0 / (2.0 * m)
+        per = []
+        with drot.Solver(device=device, **cfg) as s:
+            args = _device_problem(pr, False, device)
+            _timed_solve(s, args, rho=rho, tol=-1.0, max_iter=iters)
+            _timed_solve(s, args, rho=rho, tol=-1.0, max_iter=2 * iters)
+            for _ in range(runs):
+                _, t1 = _timed_solve(s, args, rho=rho, tol=-1.0, max_iter=iters)
+                _, t2 = _timed_solve(s, args, rho=rho, tol=-1.0, max_iter=2 * iters)
+                per.append((t2 - t1) / iters)
+            plan = s.profile()
+        per.sort()
+        med = statistics.median(per)
+        rows.append(dict(m=m, n=m, median_us=med * 1e6, lo_us=float(np.percentile(per, 2.5)) * 1e6,
+                         hi_us=float(np.percentile(per, 97.5)) * 1e6, gbs=12.0 * m * m / med / 1e9,
+                         step_variant=plan["step_variant"], tile_k=plan["tile_k"]))
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return dict(experiment="runtime", runs=runs, iters=iters, config=cfg, rows=rows)
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    a1 = sub.add_parser("e1", help="robustness profile")
+    a1.add_argument("--problems", type=int, default=100)
+    a1.add_argument("--m", type=int, default=512)
+    a1.add_argument("--sigma-t", type=float, default=5.0)
+    a1.add_argument("--f64", action="store_true")
+    a1.add_argument("--max-iter", type=int, default=1000)
+    a3 = sub.add_parser("e3", help="time to accuracy against size")
+    a3.add_argument("--sizes", type=int, nargs="+", default=[100, 512, 2000, 5000, 10000, 20000])
+    a3.add_argument("--eps", type=float, nargs="+", default=[1e-1, 1e-2, 1e-3])
+    a3.add_argument("--runs", type=int, default=3)
+    a3.add_argument("--k-cap", type=int, default=400_000)
+    ar = sub.add_parser("runtime", help="per-iteration runtime against size")
+    ar.add_argument("--sizes", type=int, nargs="+", default=[100, 200, 500, 1000, 2000, 5000, 10000, 20000])
+    ar.add_argument("--runs", type=int, default=10)
+    ar.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
+    ar.add_argument("--cluster", type=int, default=0, help="0 automatic, 1 never, 2 required")
+    for a in (a1, a3, ar):
+        a.add_argument("--out", default=None)
+        a.add_argument("--device", type=int, default=0)
+    args = ap.parse_args(argv)
+    t0 = time.time()
+    if args.cmd == "e1":
+        res = robustness(problems=args.problems, m=args.m, sigma_t=args.sigma_t, f64=args.f64,
+                         max_iter=args.max_iter, device=args.device)
+    elif args.cmd == "e3":
+        res = time_to_accuracy(sizes=args.sizes, eps_list=args.eps, runs=args.runs, k_cap=args.k_cap,
+                               device=args.device)
+    else:
+        cfg = dict(cluster=args.cluster)
+        if args.persistent:
+            cfg["persistent"] = True
+        res = runtime_per_iteration(sizes=args.sizes, runs=args.runs, device=args.device, **cfg)
+    res["wall_seconds"] = time.time() - t0
+    text = json.dumps(res)
+    if args.out:
+        with open(args.out, "w") as fh:
+            fh.write(text)
+    print(text)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
