@@ -61,26 +61,30 @@ struct Arena {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Cost model of the CTA work split over row segments (one row of one column tile).
-// A warp takes one row segment per memory round trip whatever the segment's width, so
-// a segment of w columns costs w + kRowTripCost * TW column-equivalents: its bytes
-// plus a fixed share for the round trip.  Balancing by columns alone would hand the m
-// rows of a ragged last tile of a few columns (n = 20000 leaves 32 after 39 tiles of
-// 512) to one CTA, whose m / 8 round trips per warp would then set the step's length
-// (measured on B300: 1.7 TB/s at 20000 x 20000).  3.0 was the best of 0.25 .. 8 and
-// pure row-count balancing over square, wide, tall and ragged shapes (6.1 TB/s there).
-// Entering a tile costs a CTA kTileSwitchRows full rows more: the column partials of
-// the tile it leaves are reduced and flushed, and its copy pipeline drains and refills
-// (CTAs whose range crossed a tile boundary were the last to finish, by about 5 us).
-constexpr double kRowTripCost = 3.0;
-constexpr double kTileSwitchRows = 32.0;
+// A warp takes one row segment per memory round trip whatever the segment's width (a
+// lane issues all its 16-byte loads of the row at once), so a segment of w columns
+// costs w + kRowTripCols column-equivalents: its bytes plus a fixed charge for the
+// round trip, the same for every tile width.  Balancing by columns alone would hand
+// the m rows of a ragged last tile of a few columns (n = 20000 leaves 32 after 39
+// tiles of 512) to one CTA, whose m / 8 round trips per warp would then set the
+// step's length (measured on B300: 1.7 TB/s at 20000 x 20000); in a batch it would
+// load the CTAs that hold narrow problems with several times too many rows (their
+// SMs were busy for the whole launch while the average SM idled a third of it).
+// 1536 (three 512-column rows) was the best of 0.25 .. 8 rows and pure row counting
+// over square, wide, tall and ragged shapes (6.1 TB/s at 20000 x 20000).  Entering a
+// tile costs kTileSwitchCols more, 64 full rows: the column partials of the tile a CTA
+// leaves are reduced and flushed and its copy pipeline drains and refills (CTAs whose
+// range crossed a tile boundary were the last to finish, by about 5 us, before this
+// charge; 64 rows beat 32 in a batch of 512 small problems, 3.77 vs 3.66 TB/s).
+constexpr double kRowTripCols = 1536.0;
+constexpr double kTileSwitchCols = 64.0 * (512.0 + kRowTripCols);
 
 struct SegCost {
     long long m, T, TW, last_w;
     double full, last, sw;  // cost of a row segment of a full tile / of the last tile; of a tile start
     SegCost(long long m_, long long T_, long long TW_, long long n)
-        : m(m_), T(T_), TW(TW_), last_w(n - (T_ - 1) * TW_),
-          full((1.0 + kRowTripCost) * (double)TW_), last((double)last_w + kRowTripCost * (double)TW_),
-          sw(kTileSwitchRows * full) {}
+        : m(m_), T(T_), TW(TW_), last_w(n - (T_ - 1) * TW_), full((double)TW_ + kRowTripCols),
+          last((double)last_w + kRowTripCols), sw(kTileSwitchCols) {}
     // Cost of the first u segments (tile-major order).
     double before(long long u) const {
         const long long full_units = (T - 1) * m;
@@ -1094,7 +1098,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     for (int b = 0; b < B; ++b) {
         const long long m = pr[b].m, n = pr[b].n;
         const int fb = (int)std::min<long long>(
-            64, std::max<long long>(1, (m + n + drot::kFinishThreads - 1) / drot::kFinishThreads));
+            64, std::max<long long>(1, (m + n + drot::kBatchFinishElems - 1) / drot::kBatchFinishElems));
         hp[b].fin_blocks = fb;
         FB += fb;
         off[b] = bytes;
@@ -1246,7 +1250,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         for (int it = 0; it < g && err == cudaSuccess; ++it) {
             err = launch_k(drot::drot_batched_step_kernel<true>, dim3(G), dim3(drot::kThreads), 0, h->stream, true, A);
             if (err == cudaSuccess)
-                err = launch_k(drot::drot_batched_finish_kernel, dim3(FB), dim3(drot::kFinishThreads), 0, h->stream,
+                err = launch_k(drot::drot_batched_finish_kernel, dim3(FB), dim3(drot::kBatchFinishThreads), 0, h->stream,
                                true, A);
         }
         cudaError_t endc = cudaStreamEndCapture(h->stream, &graph);

@@ -224,13 +224,19 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
 }
 
 // Steps 5-8 and the stopping test of every active problem (one block group each).
-__global__ void __launch_bounds__(kFinishThreads) drot_batched_finish_kernel(BatchArgs B) {
+// Blocks of kBatchFinishThreads threads, one per kBatchFinishElems elements of a
+// problem (four per thread): a batch of hundreds of problems would otherwise launch
+// tens of thousands of small blocks per iteration, and the block launch rate, not the
+// work, would set the finish's length (117 us per iteration for 512 problems).
+constexpr int kBatchFinishThreads = 256;
+constexpr int kBatchFinishElems = 4 * kBatchFinishThreads;
+__global__ void __launch_bounds__(kBatchFinishThreads) drot_batched_finish_kernel(BatchArgs B) {
     wait_for_predecessor();
     const int pi = B.fin_prob[blockIdx.x];
     if (pi < 0) return;
     const BatchProb& P = B.probs[pi];
     if (P.sc->done != kRunning) return;
-    finish_body(batch_finish_args(P), B.fin_local[blockIdx.x], P.fin_blocks);
+    finish_body<kBatchFinishThreads>(batch_finish_args(P), B.fin_local[blockIdx.x], P.fin_blocks);
 }
 
 // a_0, b_0, alpha_0 and the numerators of phi_0, psi_0 of every active problem.

@@ -1028,33 +1028,56 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
     // acc: 0 sum r, 1 ||r||_1 + ||s||_1, 2 ||r||^2 + ||s||^2, 3 p.g', 4 q.h', 5 sum s
     double acc[kFinishAcc] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const long long mn = A.m + A.n;
-    for (long long idx = (long long)blk * NT + threadIdx.x; idx < mn; idx += (long long)nblk * NT) {
-        if (idx < A.m) {
-            const long long i = idx;
-            const double pi = pre.valid ? pre.pq : A.p[i];
-            const double ai = pre.valid ? pre.ab : __ldcg(A.a + i);
-            const double r = row_total(A, i) - pi;
-            const double gn = ai - 2.0 * r;
-            A.a[i] = ai - r;
-            A.g[i] = gn;
-            acc[0] += r;
-            acc[1] += fabs(r);
-            acc[2] += r * r;
-            acc[3] += pi * gn;
-        } else {
-            const long long j = idx - A.m;
-            const double qj = pre.valid ? pre.pq : A.q[j];
-            const double bj = pre.valid ? pre.ab : __ldcg(A.b + j);
-            const double s = col_total(A, j) - qj;
-            const double hn = bj - 2.0 * s;
-            A.b[j] = bj - s;
-            A.h[j] = hn;
-            acc[5] += s;
-            acc[1] += fabs(s);
-            acc[2] += s * s;
-            acc[4] += qj * hn;
+    // E elements per thread per pass, all their loads issued before any store (a store
+    // to a, g, u could alias a later load as far as the compiler knows, which would
+    // otherwise serialise one memory round trip per element)
+    constexpr int E = 4;
+    const long long stride = (long long)nblk * NT;
+    for (long long base = (long long)blk * NT + threadIdx.x; base < mn; base += E * stride) {
+        double tot[E], pq[E], ab[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const long long idx = base + e * stride;
+            tot[e] = pq[e] = ab[e] = 0.0;
+            if (idx < A.m) {
+                tot[e] = A.accumulate ? __ldcg(A.u + idx) : row_total(A, idx);
+                pq[e] = (e == 0 && pre.valid) ? pre.pq : A.p[idx];
+                ab[e] = (e == 0 && pre.valid) ? pre.ab : __ldcg(A.a + idx);
+            } else if (idx < mn) {
+                const long long j = idx - A.m;
+                tot[e] = A.accumulate ? __ldcg(A.v + j) : col_total(A, j);
+                pq[e] = (e == 0 && pre.valid) ? pre.pq : A.q[j];
+                ab[e] = (e == 0 && pre.valid) ? pre.ab : __ldcg(A.b + j);
+            }
         }
         pre.valid = false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const long long idx = base + e * stride;
+            if (idx < A.m) {
+                const long long i = idx;
+                if (A.accumulate) A.u[i] = 0.0;  // the totals start from zero in the next step
+                const double r = tot[e] - pq[e];
+                const double gn = ab[e] - 2.0 * r;
+                A.a[i] = ab[e] - r;
+                A.g[i] = gn;
+                acc[0] += r;
+                acc[1] += fabs(r);
+                acc[2] += r * r;
+                acc[3] += pq[e] * gn;
+            } else if (idx < mn) {
+                const long long j = idx - A.m;
+                if (A.accumulate) A.v[j] = 0.0;
+                const double sj = tot[e] - pq[e];
+                const double hn = ab[e] - 2.0 * sj;
+                A.b[j] = ab[e] - sj;
+                A.h[j] = hn;
+                acc[5] += sj;
+                acc[1] += fabs(sj);
+                acc[2] += sj * sj;
+                acc[4] += pq[e] * hn;
+            }
+        }
     }
     if (A.accumulate) {
 #pragma unroll
