@@ -159,7 +159,7 @@ ClusterPlan cluster_plan(long long m, long long n) {
         if (m < cs || n < cs) continue;
         const int R = (int)((m + cs - 1) / cs), Q = (int)((n + cs - 1) / cs);
         const int npad = (int)((n + 3) / 4 * 4);
-        const size_t bytes = drot::cluster_smem_bytes(R, Q, npad, n);
+        const size_t bytes = drot::cluster_smem_bytes(R, Q, npad, n, cs);
         if (bytes <= kClusterSmemMax) {
             cp.cs = cs;
             cp.R = R;

@@ -9,9 +9,14 @@
 // order the exchange.  Every CTA then forms the same scalar totals in the same order,
 // so all CTAs take the same stopping decision and leave the loop together.
 //
-// Shared buffers written in one iteration and read remotely are double-buffered by
-// iteration parity: a CTA can overwrite buffer k & 1 only after the barrier of
-// iteration k + 1 that every CTA reaches after its last remote read of iteration k.
+// Exchanges are pushed, not pulled: a CTA stores its column partials into the owners'
+// shared memory, and its partial totals and its new h_j into every CTA's, before the
+// cluster barrier that publishes them (barrier.cluster arrive has release and wait has
+// acquire semantics), so every read on the critical path is local.  No double
+// buffering is needed: each inbox is next written only after a barrier that every CTA
+// reaches after its last read of it (column partials: written in phase 1, read in
+// phase 2, rewritten after barrier #2; totals and h: written in phase 2, read in
+// phase 3, rewritten after the next barrier #1).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -43,29 +48,31 @@ struct ClusterSmem {
     float* Xs;      // [R][npad]
     float* Cs;      // [R][npad]
     float* psi;     // [npad]   psi_j (FP32) for all columns
-    double* colp;   // [2][n]   this CTA's column partials, by iteration parity
-    double* hown;   // [2][Q]   h_j of the owned columns (read remotely), by parity
-    double* part;   // [2][kClusterParts] this CTA's scalar partials, by parity
+    double* colin;  // [CS][Q]  column partials of the owned columns, pushed by every CTA (rank-major)
+    double* partin; // [CS][kClusterParts] scalar partials, pushed by every CTA (rank-major)
     double* u;      // [R]      row sums of the owned rows
     double* arow;   // [R]      a_i of the owned rows
     double* grow;   // [R]      g_i of the owned rows
     double* bcol;   // [Q]      b_j of the owned columns
-    double* hall;   // [n]      h_j of all columns
+    double* hall;   // [n]      h_j of all columns (pushed by their owners)
     double* red;    // [kClusterThreads / 32][kClusterParts] block reduction scratch
+    double* prow;   // [R]      p_i of the owned rows
+    double* qcol;   // [Q]      q_j of the owned columns
 };
 
-__host__ __device__ inline size_t cluster_smem_bytes(int R, int Q, int npad, long long n) {
+__host__ __device__ inline size_t cluster_smem_bytes(int R, int Q, int npad, long long n, int cs) {
     size_t b = 0;
     b += 2 * (size_t)R * npad * sizeof(float);
     b += (size_t)npad * sizeof(float);
     b = (b + 15) / 16 * 16;
-    b += 2 * (size_t)n * sizeof(double) + 2 * (size_t)Q * sizeof(double) + 2 * kClusterParts * sizeof(double);
+    b += (size_t)cs * Q * sizeof(double) + (size_t)cs * kClusterParts * sizeof(double);
     b += 2 * (size_t)R * sizeof(double) + (size_t)R * sizeof(double) + (size_t)Q * sizeof(double);
     b += (size_t)n * sizeof(double) + (kClusterThreads / 32) * kClusterParts * sizeof(double);
+    b += (size_t)R * sizeof(double) + (size_t)Q * sizeof(double);
     return b;
 }
 
-__device__ inline ClusterSmem carve_cluster_smem(unsigned char* base, int R, int Q, int npad, long long n) {
+__device__ inline ClusterSmem carve_cluster_smem(unsigned char* base, int R, int Q, int npad, long long n, int cs) {
     ClusterSmem S;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -77,15 +84,16 @@ __device__ inline ClusterSmem carve_cluster_smem(unsigned char* base, int R, int
     S.Cs = reinterpret_cast<float*>(take((size_t)R * npad * sizeof(float)));
     S.psi = reinterpret_cast<float*>(take((size_t)npad * sizeof(float)));
     off = (off + 15) / 16 * 16;
-    S.colp = reinterpret_cast<double*>(take(2 * (size_t)n * sizeof(double)));
-    S.hown = reinterpret_cast<double*>(take(2 * (size_t)Q * sizeof(double)));
-    S.part = reinterpret_cast<double*>(take(2 * kClusterParts * sizeof(double)));
+    S.colin = reinterpret_cast<double*>(take((size_t)cs * Q * sizeof(double)));
+    S.partin = reinterpret_cast<double*>(take((size_t)cs * kClusterParts * sizeof(double)));
     S.u = reinterpret_cast<double*>(take((size_t)R * sizeof(double)));
     S.arow = reinterpret_cast<double*>(take((size_t)R * sizeof(double)));
     S.grow = reinterpret_cast<double*>(take((size_t)R * sizeof(double)));
     S.bcol = reinterpret_cast<double*>(take((size_t)Q * sizeof(double)));
     S.hall = reinterpret_cast<double*>(take((size_t)n * sizeof(double)));
     S.red = reinterpret_cast<double*>(take((kClusterThreads / 32) * kClusterParts * sizeof(double)));
+    S.prow = reinterpret_cast<double*>(take((size_t)R * sizeof(double)));
+    S.qcol = reinterpret_cast<double*>(take((size_t)Q * sizeof(double)));
     return S;
 }
 
@@ -96,7 +104,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int R = P.rows_per_cta, Q = P.cols_per_cta, npad = P.npad;
     const long long m = P.m, n = P.n;
-    ClusterSmem S = carve_cluster_smem(smem_raw, R, Q, npad, n);
+    ClusterSmem S = carve_cluster_smem(smem_raw, R, Q, npad, n, CS);
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long r0 = (long long)rank * R;
@@ -113,8 +121,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
     for (int i = tid; i < nrows; i += kClusterThreads) {
         S.arow[i] = P.a[r0 + i];
         S.grow[i] = P.g[r0 + i];
+        S.prow[i] = P.p[r0 + i];
     }
-    for (int j = tid; j < ncols; j += kClusterThreads) S.bcol[j] = P.b[c0 + j];
+    for (int j = tid; j < ncols; j += kClusterThreads) {
+        S.bcol[j] = P.b[c0 + j];
+        S.qcol[j] = P.q[c0 + j];
+    }
     for (long long j = tid; j < n; j += kClusterThreads) S.hall[j] = P.h[j];
     const double rho = P.sc->rho, inv_rho = P.sc->inv_rho, tol = P.sc->tol;
     const double sum_p = P.sc->sum_p, sum_q = P.sc->sum_q;
@@ -131,8 +143,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
     __syncthreads();
 
     for (long long it = 0; it < P.budget && done == kRunning; ++it) {
-        const int buf = (int)(it & 1);
-        double* colp = S.colp + (size_t)buf * n;
         // ---- phase 1: step 4 on the owned rows, with row sums, column partials, <C,X>, dual residual
         float scx = 0.f, sd = 0.f;
         for (int i = warp; i < nrows; i += kClusterThreads / 32) {
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
         }
         __syncthreads();
         // column partials: thread per column; runs of 16 rows in FP32, promoted to FP64
-        // (FP64 has a long dependent latency on this GPU)
+        // (FP64 has a long dependent latency on this GPU); pushed to the column's owner
         for (long long j = tid; j < n; j += kClusterThreads) {
             double v = 0.0;
             for (int i0 = 0; i0 < nrows; i0 += 16) {
@@ -162,7 +172,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
                 for (int i = i0; i < min(nrows, i0 + 16); ++i) f += S.Xs[(size_t)i * npad + j];
                 v += (double)f;
             }
-            colp[j] = v;
+            const int owner = (int)(j / Q);
+            cluster.map_shared_rank(S.colin, owner)[(size_t)rank * Q + (j - (long long)owner * Q)] = v;
         }
         // CTA totals of <C,X> and sum [d]_+^2 (warp sums in FP32, then FP64 across warps)
         scx = warp_sum_f32(scx);
@@ -174,66 +185,74 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
         cluster.sync();  // #1: every CTA's column partials are ready
 
         // ---- phase 2: steps 5-8 for the owned rows and columns, CTA partials of the totals
-        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // sum r, l1, l2^2, p.g, q.h, sum s
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // sum r, l1, l2^2, p.g, q.h, sum s
         for (int i = tid; i < nrows; i += kClusterThreads) {
-            const double r = S.u[i] - P.p[r0 + i];
+            const double pi = S.prow[i];
+            const double r = S.u[i] - pi;
             const double gn = S.arow[i] - 2.0 * r;
             S.arow[i] -= r;
             S.grow[i] = gn;
             acc[0] += r;
             acc[1] += fabs(r);
             acc[2] += r * r;
-            acc[3] += P.p[r0 + i] * gn;
+            acc[3] += pi * gn;
         }
-        double* hown = S.hown + (size_t)buf * Q;
-        for (int jj = tid; jj < ncols; jj += kClusterThreads) {
-            const long long j = c0 + jj;
-            double v4[4] = {0.0, 0.0, 0.0, 0.0};  // four chains, combined in a fixed order
+        // columns: a group of CS lanes per column, lane g holding the partial pushed by
+        // CTA g; a shuffle tree inside the group adds them (log2 CS dependent FP64 adds)
+        // and the group's first lane finishes the column and pushes h_j to every CTA
+        {
+            constexpr int GPW = 32 / CS;  // columns per warp per pass
+            const int g = lane % CS;
+            for (int jj0 = warp * GPW; jj0 < ncols; jj0 += (kClusterThreads / 32) * GPW) {  // warp-uniform
+                const int jj = jj0 + lane / CS;
+                double v = jj < ncols ? S.colin[(size_t)g * Q + jj] : 0.0;
 #pragma unroll
-            for (int rr = 0; rr < CS; ++rr) v4[rr & 3] += cluster.map_shared_rank(colp, rr)[j];
-            const double v = (v4[0] + v4[1]) + (v4[2] + v4[3]);
-            const double s = v - P.q[j];
-            const double hn = S.bcol[jj] - 2.0 * s;
-            S.bcol[jj] -= s;
-            hown[jj] = hn;
-            acc[5] += s;
-            acc[1] += fabs(s);
-            acc[2] += s * s;
-            acc[4] += P.q[j] * hn;
+                for (int o = CS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (g == 0 && jj < ncols) {
+                    const long long j = c0 + jj;
+                    const double qj = S.qcol[jj];
+                    const double sj = v - qj;
+                    const double hn = S.bcol[jj] - 2.0 * sj;
+                    S.bcol[jj] -= sj;
+#pragma unroll
+                    for (int rr = 0; rr < CS; ++rr) cluster.map_shared_rank(S.hall, rr)[j] = hn;
+                    acc[5] += sj;
+                    acc[1] += fabs(sj);
+                    acc[2] += sj * sj;
+                    acc[4] += qj * hn;
+                }
+            }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int q2 = 0; q2 < 6; ++q2) acc[q2] += __shfl_xor_sync(0xffffffffu, acc[q2], o);
-        if (lane == 0)
-#pragma unroll
-            for (int q2 = 0; q2 < 6; ++q2) S.red[warp * kClusterParts + 2 + q2] = acc[q2];
+        {
+            const double tot_l = warp_sum8_scatter(acc);  // lane 4q holds the warp total of value q
+            const int qv = (lane >> 2) & 7;
+            if ((lane & 3) == 0 && qv < 6) S.red[warp * kClusterParts + 2 + qv] = tot_l;
+        }
         __syncthreads();
-        double* part = S.part + (size_t)buf * kClusterParts;
         if (tid < kClusterParts) {
             double v = 0.0;
             for (int w = 0; w < kClusterThreads / 32; ++w) v += S.red[w * kClusterParts + tid];
-            // part layout: 0 sum r, 1 l1, 2 l2^2, 3 p.g, 4 q.h, 5 sum s, 6 <C,X>, 7 sum [d]_+^2
+            // partial layout: 0 sum r, 1 l1, 2 l2^2, 3 p.g, 4 q.h, 5 sum s, 6 <C,X>, 7 sum [d]_+^2
             const int dst = tid < 2 ? 6 + tid : tid - 2;
-            part[dst] = v;
+#pragma unroll
+            for (int rr = 0; rr < CS; ++rr) cluster.map_shared_rank(S.partin, rr)[rank * kClusterParts + dst] = v;
         }
-        cluster.sync();  // #2: every CTA's partials and owned h_j are ready
+        cluster.sync();  // #2: every CTA holds all partials and all h_j
 
-        // ---- phase 3 (every CTA, identically): totals, scalars, stopping test, h of all columns.
-        // Warp 0 gathers the CS partials (lane r reads CTA r), reduces them with a fixed
-        // shuffle pattern and lane 0 updates the scalars; the same code on the same data in
+        // ---- phase 3 (every CTA, identically): totals, scalars, stopping test, psi.
+        // Warp 0 takes the CS partials (lane r those of CTA r), reduces them with a fixed
+        // reduce-scatter pattern and lane 0 updates the scalars; the same code on the same data in
         // every CTA gives bitwise the same result everywhere.  Broadcast through shared memory.
         __shared__ double s_bc[4];
         __shared__ int s_done;
         if (warp == 0) {
             double t[kClusterParts];
-            const double* rp = cluster.map_shared_rank(part, lane < CS ? lane : 0);
+            const double* rp = S.partin + (size_t)(lane < CS ? lane : 0) * kClusterParts;
 #pragma unroll
             for (int q2 = 0; q2 < kClusterParts; ++q2) t[q2] = lane < CS ? rp[q2] : 0.0;
+            const double tq = warp_sum8_scatter(t);  // lane 4q holds total q
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int q2 = 0; q2 < kClusterParts; ++q2) t[q2] += __shfl_down_sync(0xffffffffu, t[q2], o);
+            for (int q2 = 0; q2 < kClusterParts; ++q2) t[q2] = __shfl_sync(0xffffffffu, tq, 4 * q2);
             if (lane == 0) {
                 beta = t[0] * P.inv_mn;
                 const double c_new = 2.0 * beta - alpha;
@@ -267,12 +286,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
         beta = s_bc[2];
         done = s_done;
         k += 1;
-        // h of all columns from their owners, then psi for the next pass
-        for (long long j = tid; j < n; j += kClusterThreads) {
-            const int owner = (int)(j / Q);
-            S.hall[j] = cluster.map_shared_rank(S.hown + (size_t)buf * Q, owner)[j - (long long)owner * Q];
-        }
-        __syncthreads();
+        // psi for the next pass
         for (long long j = tid; j < n; j += kClusterThreads) S.psi[j] = (float)((S.hall[j] + c) * P.inv_m);
         __syncthreads();
     }

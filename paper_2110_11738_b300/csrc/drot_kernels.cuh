@@ -114,6 +114,35 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
+// Warp-wide sums of eight FP64 values per lane with nine FP64 additions per lane, in a
+// fixed order (a reduce-scatter butterfly): at offsets 16, 8 and 4 a lane keeps half
+// of its running values, receives its partner's copies of them and adds; offsets 2
+// and 1 finish the one value left.  Lane l returns the warp total of value
+// (l >> 2) & 7.  A plain shuffle tree would take 8 x 5 = 40 additions; a dependent
+// FP64 add is slow on this GPU, so the tree sat on the critical path of every finish.
+__device__ __forceinline__ double warp_sum8_scatter(const double (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+    double k4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double keep = b4 ? v[4 + i] : v[i];
+        const double give = b4 ? v[i] : v[4 + i];
+        k4[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+    double k2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double keep = b3 ? k4[2 + i] : k4[i];
+        const double give = b3 ? k4[i] : k4[2 + i];
+        k2[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    double k1 = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? k2[0] : k2[1], 4);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+    return k1;
+}
+
 // Partial-sum sinks of the fused step.  Fixed-order mode writes one partial per
 // (column tile, row), per (CTA, tile) and per CTA, each with a single writer, for
 // the finish kernel to add in a fixed order (bitwise reproducible).  Accumulation
@@ -1080,16 +1109,14 @@ __device__ __forceinline__ void finish_body(const FinishArgs& A, int blk, int nb
         }
     }
     if (A.accumulate) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int c = 0; c < kFinishAcc; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-        if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-            for (int c = 0; c < kFinishAcc; ++c) s_red[threadIdx.x >> 5][c] = acc[c];
-        }
+        const double v8[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], 0.0, 0.0};
+        const double tot_l = warp_sum8_scatter(v8);  // lane 4q holds the warp total of value q
+        const int q = (threadIdx.x >> 2) & 7;
+        if ((threadIdx.x & 3) == 0 && q < kFinishAcc) s_red[threadIdx.x >> 5][q] = tot_l;
         __syncthreads();
         if (threadIdx.x != 0) return;
+#pragma unroll
+        for (int c = 0; c < kFinishAcc; ++c) acc[c] = s_red[0][c];
 #pragma unroll
         for (int w = 1; w < NT / 32; ++w)
 #pragma unroll
