@@ -76,8 +76,22 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch(workload):
-    """DRAM bytes per fused-step launch from the committed ncu summary, if it is current."""
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth (context beside the measured copy peak)
+
+
+def _step_kernel_name(prof, c_skip):
+    """Name of the fused-step kernel the solve ran, from the plan it reports."""
+    v, k, st = prof["step_variant"], prof["tile_k"], prof["stages"]
+    if c_skip:
+        return f"drot_step_kernel<{k},1,1|2>"
+    return {1: f"drot_step_kernel<{k},1,0>", 2: f"drot_step_tma_kernel<{k},{st}>",
+            3: f"drot_step_async_kernel<{k},{st}>", 4: f"drot_cluster_kernel<{st}>",
+            5: "drot_step_f64_kernel<1>"}.get(v, f"variant {v}")
+
+
+def _traffic_per_launch(workload, kernel=None):
+    """DRAM bytes per fused-step launch from the committed ncu summary, if it is current
+    (same kernel source) and was taken on the kernel that ran."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as fh:
@@ -87,7 +101,9 @@ def _traffic_per_launch(workload):
     if d.get("kernel_source_sha256_16") != _kernel_source_hash():
         return None
     rec = d.get("workloads", {}).get(workload)
-    return None if rec is None else float(rec["dram_bytes_per_launch"])
+    if rec is None or (kernel is not None and rec.get("kernel") != kernel):
+        return None
+    return float(rec["dram_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -324,7 +340,8 @@ def run_ours(args):
         except MemoryError:
             cpu = None
 
-    traffic = _traffic_per_launch(args.workload)
+    kernel_name = _step_kernel_name(pprof, args.c_skip)
+    traffic = _traffic_per_launch(args.workload, kernel_name)
     line = {
         "metric": METRIC,
         "value": ms_per_solve / 1e3,
@@ -351,7 +368,8 @@ def run_ours(args):
         "ms_per_iter": ms_per_solve / statistics.mean(iters),
         "gpu_launches": int(prof["kernel_launches"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind, "kernel": "drot_step_kernel",
+                     "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                      "step_ms": step_ms, "timed_launches": int(pprof["step_launches"]),
                      "finish_ms": pprof["finish_ms_total"] / max(1, pprof["step_launches"]),
                      "step_plus_finish_ms": pprof["iter_ms_total"] / max(1, pprof["step_launches"]),
