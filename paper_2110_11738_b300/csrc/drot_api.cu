@@ -309,7 +309,8 @@ struct drot_handle {
     Arena batch;                        // per-problem vectors, scalars and work lists
     Scalars *h_bstat = nullptr;         // pinned read-back of every problem's scalars
     size_t h_bstat_cap = 0;
-    int batch_k_thresholds[2] = {0, 0};  // autotuned tile policy: K = 1 below t0, 2 below t1, else 4
+    int batch_k_thresholds[2] = {-1, -1};  // tile policy of the last tuned batch: K = 1 below t0, 2 below t1, else 4
+    unsigned long long batch_tuned_sig = 0;  // shape signature of that batch (0: none)
 };
 
 namespace {
@@ -1019,6 +1020,31 @@ struct BatchLists {
 // Tile width policy: K = 1 for n < t0, 2 for n < t1, else 4.
 int batch_k(long long n, const int thr[2]) { return n < thr[0] ? 1 : (n < thr[1] ? 2 : 4); }
 
+// Tile policies the batched autotuner times: (t0, t1) thresholds of batch_k.  The first
+// (512-column tiles for every problem) is the default: in a batch of 512 problems of
+// sizes 64 .. 2048 it ran an all-active iteration in 1.52 ms against 1.85 ms for the
+// width-matched policy (384, 1536), because a warp keeps one row segment in flight per
+// round trip and wider segments move more bytes per trip, ragged tails included.
+constexpr int kBatchPolicies[][2] = {{0, 0}, {384, 384}, {384, 1024}, {384, 1536}};
+
+// A signature of a batch's shapes (FNV-1a over m, n): the autotuned policy is reused
+// while the shapes stay the same.
+unsigned long long batch_signature(const drot_problem *pr, int B) {
+    unsigned long long x = 1469598103934665603ull;
+    auto mix = [&](unsigned long long v) {
+        for (int i = 0; i < 8; ++i) {
+            x ^= (v >> (8 * i)) & 0xffull;
+            x *= 1099511628211ull;
+        }
+    };
+    mix((unsigned long long)B);
+    for (int b = 0; b < B; ++b) {
+        mix((unsigned long long)pr[b].m);
+        mix((unsigned long long)pr[b].n);
+    }
+    return x ? x : 1ull;
+}
+
 // Segment list, cost-balanced CTA ranges (SegCost) and finish-block groups of the active problems.
 void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector<int> &active, int G, int FB,
                        BatchLists &L) {
@@ -1085,8 +1111,10 @@ drot_status upload_lists(drot_handle *h, const BatchLists &L, const BatchDev &D,
 drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, double tol, long long max_iter,
                                  int warm, drot_result *res) {
     const int rule = (h->cfg.stop_rule & 7) ? (h->cfg.stop_rule & 7) : (DROT_STOP_GAP | DROT_STOP_RES_L1);
-    int thr[2] = {384, 1536};
-    if (h->batch_k_thresholds[0] > 0) {
+    int thr[2] = {kBatchPolicies[0][0], kBatchPolicies[0][1]};
+    const unsigned long long sig = batch_signature(pr, B);
+    const bool tuned = h->cfg.autotune && h->batch_tuned_sig == sig;
+    if (tuned) {
         thr[0] = h->batch_k_thresholds[0];
         thr[1] = h->batch_k_thresholds[1];
     }
@@ -1193,6 +1221,80 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     }
     const int nvalid = (int)valid.size();
 
+    drot::BatchArgs A{};
+    A.probs = D.probs;
+    A.active = D.active;
+    A.unit0 = D.unit0;
+    A.wbound = D.wbound;
+    A.fin_prob = D.fin_prob;
+    A.fin_local = D.fin_local;
+    A.nactive = D.nactive;
+    A.warm = warm;
+
+    // Tile policy autotuning (autotune = 1, cold starts, a batch shape not tuned yet):
+    // time the fused step of this batch under every candidate policy, one warm-up and
+    // three launches each, before X_0 is written (the launches run on the caller's X,
+    // which the cold start overwrites next), then zero the totals they touched.
+    if (h->cfg.autotune && !warm && nvalid > 0 && !tuned) {
+        cudaEvent_t e0, e1;
+        DROT_CUDA(h, cudaEventCreate(&e0));
+        DROT_CUDA(h, cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_p = 0;
+        drot_status tst = DROT_OK;
+        const int npol = (int)(sizeof(kBatchPolicies) / sizeof(kBatchPolicies[0]));
+        for (int pi = 0; pi < npol && tst == DROT_OK; ++pi) {
+            for (int b = 0; b < B; ++b) {
+                hp[b].K = batch_k(hp[b].n, kBatchPolicies[pi]);
+                hp[b].T = (int)((hp[b].n + 128LL * hp[b].K - 1) / (128LL * hp[b].K));
+            }
+            cudaError_t e = cudaMemcpyAsync(D.probs, hp.data(), sizeof(drot::BatchProb) * B, cudaMemcpyHostToDevice,
+                                            h->stream);
+            if (e != cudaSuccess) {
+                tst = fail(h, DROT_ERR_CUDA, "tuning upload failed: %s", cudaGetErrorString(e));
+                break;
+            }
+            BatchLists TL;
+            build_batch_lists(hp, valid, G, FB, TL);
+            tst = upload_lists(h, TL, D, FB);
+            if (tst != DROT_OK) break;
+            drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(A);
+            e = cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(A);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                tst = fail(h, DROT_ERR_CUDA, "tuning launch failed: %s", cudaGetErrorString(e));
+                break;
+            }
+            h->prof.kernel_launches += 4;
+            if (ms < best) {
+                best = ms;
+                best_p = pi;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (tst != DROT_OK) return tst;
+        thr[0] = kBatchPolicies[best_p][0];
+        thr[1] = kBatchPolicies[best_p][1];
+        h->batch_k_thresholds[0] = thr[0];
+        h->batch_k_thresholds[1] = thr[1];
+        h->batch_tuned_sig = sig;
+        for (int b = 0; b < B; ++b) {
+            hp[b].K = batch_k(hp[b].n, thr);
+            hp[b].T = (int)((hp[b].n + 128LL * hp[b].K - 1) / (128LL * hp[b].K));
+        }
+        DROT_CUDA(h, cudaMemcpyAsync(D.probs, hp.data(), sizeof(drot::BatchProb) * B, cudaMemcpyHostToDevice,
+                                     h->stream));
+        DROT_CUDA(h, cudaMemsetAsync(base + align_up(sizeof(Scalars) * B, 256), 0, vec_bytes, h->stream));
+    }
+
     // cold start X_0 = p q^T, sums of X_0, a_0 / b_0 / alpha_0
     std::vector<int> flags(B, 0);
     for (int b : valid) flags[b] = warm ? 0 : 1;
@@ -1206,15 +1308,6 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     build_batch_lists(hp, valid, G, FB, L);
     st = upload_lists(h, L, D, FB);
     if (st != DROT_OK) return st;
-    drot::BatchArgs A{};
-    A.probs = D.probs;
-    A.active = D.active;
-    A.unit0 = D.unit0;
-    A.wbound = D.wbound;
-    A.fin_prob = D.fin_prob;
-    A.fin_local = D.fin_local;
-    A.nactive = D.nactive;
-    A.warm = warm;
     drot::drot_batched_step_kernel<false><<<G, drot::kThreads, 0, h->stream>>>(A);
     DROT_CUDA(h, cudaGetLastError());
     drot::drot_batched_init_state_kernel<<<FB, drot::kFinishThreads, 0, h->stream>>>(A);

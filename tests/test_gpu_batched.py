@@ -108,3 +108,30 @@ def test_batched_uneven_config_subset_iteration_cap():
             assert abs(r["res_l1"] - one["res_l1"]) <= 1e-4 * one["res_l1"] + 1e-9
             S = pr.rho * 4
             assert float((P["X"] - Q["X"]).abs().max()) <= 8 * EPS32 * S * 200
+
+
+def test_batched_autotuned_tiles_keep_parity():
+    """The tile-policy autotuner times the step on the caller's X before the cold start
+    writes X_0 and then zeroes the totals it touched: the solve must agree with the
+    untuned one, problem by problem, and a warm batch on the same handle must be untouched."""
+    specs = workloads.make_batch(B=16, seed=5)
+    with drot.Solver(device=0) as s:
+        base = [_dev_problem(pr) for pr in specs]
+        ref = s.solve_batched(base, tol=-1.0, max_iter=150)
+    with drot.Solver(device=0, autotune=True) as s:
+        for _ in range(2):  # the second call reuses the tuned policy
+            probs = [_dev_problem(pr) for pr in specs]
+            for P in probs:
+                P["X"].fill_(float("nan"))  # whatever X holds before a cold start is overwritten
+            res = s.solve_batched(probs, tol=-1.0, max_iter=150)
+            for pr, P, r, r0, B0 in zip(specs, probs, res, ref, base):
+                assert r["iters"] == 150
+                assert abs(r["primal_obj"] - r0["primal_obj"]) <= 1e-5 * abs(r0["primal_obj"])
+                assert abs(r["res_l1"] - r0["res_l1"]) <= 1e-4 * r0["res_l1"] + 1e-9
+                assert float((P["X"] - B0["X"]).abs().max()) <= 8 * EPS32 * pr.rho * 4 * 150
+        # warm start from the untuned results: no tuning launches touch the given X
+        warm = [dict(P, X=P["X"].clone(), mu=P["mu"].clone(), nu=P["nu"].clone()) for P in base]
+        X_in = [P["X"].clone() for P in warm]
+        res_w = s.solve_batched(warm, tol=-1.0, max_iter=0, warm=True)
+        for P, X0 in zip(warm, X_in):
+            assert torch.equal(P["X"], X0)
