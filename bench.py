@@ -163,6 +163,19 @@ def _dist():
     return world, rank, local
 
 
+def _max_over_ranks(x, world, device):
+    """The largest x over all ranks of the default process group (x itself on one rank):
+    the job's time is that of its slowest replica."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _cpu_baseline(workload, seed, iters_to_tol, sample_iters):
     """The FP64 oracle as it stands, single-threaded, on `sample_iters` iterations of the full problem."""
     import numpy as np
@@ -277,11 +290,7 @@ def run_ours(args):
     elapsed_ms = ev0.elapsed_time(ev1)
     prof = solver.profile()
 
-    t_local = elapsed_ms / args.steps
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_per_solve = float(t.item())
+    ms_per_solve = _max_over_ranks(elapsed_ms / args.steps, world, dev)
     iters = [r["iters"] for r in results]
     statuses = sorted({r["status_name"] for r in results})
 
@@ -323,10 +332,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         e_res = [host_call() for _ in range(max(1, args.e2e_steps))]
         e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.e2e_steps)
-        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": float(te.item()) / 1e3, "unit": "s",
+        e2e = {"value": _max_over_ranks(e_ms, world, dev) / 1e3, "unit": "s",
                "h2d_bytes_per_step": int(Ch.numel() * 4 + ph.numel() * 8 + qh.numel() * 8),
                "d2h_bytes_per_step": int(Xh.numel() * 4 + muh.numel() * 8 + nuh.numel() * 8),
                "iters": [r["iters"] for r in e_res]}
