@@ -115,6 +115,11 @@ typedef struct {
                                    C-reading iterations are written).  NULL: no trace.  Setting it keeps
                                    the automatic choice off the cluster-resident path, which has none */
     int64_t trace_len;
+    int64_t wait_limit;         /* polls before a grid-barrier wait of the persistent solve gives up
+                                   (0: 2^24, about a second); the first CTA to give up sets a fault flag
+                                   that makes every other CTA leave, and the solve returns
+                                   DROT_ERR_TIMEOUT with the context intact.  A small value makes the
+                                   barriers give up at once: it exists to test that path */
 } drot_config;
 
 typedef struct {

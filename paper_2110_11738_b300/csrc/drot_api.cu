@@ -500,6 +500,11 @@ drot_status setup_workspace(drot_handle *h, long long m, long long n, const Plan
     h->acc = carve<double>(cur, (size_t)drot::kAccSlots * drot::kAccStride);
     h->gsync = carve<drot::GridSync>(cur, 1);
     DROT_CUDA(h, cudaMemsetAsync(h->gsync, 0, sizeof(drot::GridSync), h->stream));
+    if (h->cfg.wait_limit > 0) {
+        const unsigned long long lim = (unsigned long long)h->cfg.wait_limit;
+        DROT_CUDA(h, cudaMemcpyAsync(&h->gsync->spin_limit, &lim, sizeof lim, cudaMemcpyHostToDevice, h->stream));
+        DROT_CUDA(h, cudaStreamSynchronize(h->stream));  // lim lives on this stack frame
+    }
     if (P.accumulate) {
         // totals start at zero; every finish pass resets what it reads
         DROT_CUDA(h, cudaMemsetAsync(h->u, 0, sizeof(double) * m, h->stream));

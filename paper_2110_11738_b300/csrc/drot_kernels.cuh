@@ -1176,7 +1176,8 @@ __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs 
 // One cooperative launch (every CTA resident) runs up to `budget` iterations:
 // fused step -> grid barrier -> finish (elements spread over all CTAs, scalar part
 // in the last CTA to arrive) -> grid barrier.  The grid barrier is a counter and a
-// generation word; a CTA that waits longer than kBarrierSpins polls records a
+// generation word; a CTA that waits longer than kBarrierSpins polls (or the solve's
+// configured limit, GridSync::spin_limit) records a
 // fault in Scalars and leaves, and every other CTA then leaves at its next wait,
 // so a broken launch ends instead of hanging.
 
@@ -1185,8 +1186,9 @@ constexpr unsigned long long kBarrierSpins = 1ull << 24;
 struct GridSync {
     unsigned int count;
     unsigned int gen;
-    unsigned long long step_ns;  // time from each step's start to the end of its barrier (CTA 0)
-    unsigned long long iters;    // iterations timed
+    unsigned long long step_ns;     // time from each step's start to the end of its barrier (CTA 0)
+    unsigned long long iters;       // iterations timed
+    unsigned long long spin_limit;  // polls before a barrier wait gives up (0: kBarrierSpins)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1211,9 +1213,10 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, Scalars* sc) {
             __threadfence();
             atomicAdd(&gs->gen, 1u);
         } else {
+            const unsigned long long limit = gs->spin_limit ? gs->spin_limit : kBarrierSpins;
             unsigned long long spins = 0;
             while (*gen == my_gen) {
-                if (++spins > kBarrierSpins || ((spins & 255ull) == 0 && *fault)) {
+                if (++spins > limit || ((spins & 255ull) == 0 && *fault)) {
                     atomicExch(&sc->fault, 1);
                     ok = 0;
                     break;
