@@ -71,8 +71,8 @@ def _step_parity(solver, pr, k, seed, stats_k=None):
     return out
 
 
-@pytest.mark.parametrize("m,n", [(1, 1), (1, 5), (3, 7), (33, 129), (130, 257), (257, 1031), (300, 2053),
-                                 (64, 4100), (17, 3)])
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 5), (2, 2), (3, 7), (2, 31), (31, 33), (33, 129), (130, 257),
+                                 (257, 1031), (300, 2053), (64, 4100), (17, 3)])
 @pytest.mark.parametrize("k", [1, 3])
 @pytest.mark.parametrize("cluster", [0, 1])  # automatic choice (cluster-resident when it fits) / streaming path
 def test_step_parity_small_and_ragged(m, n, k, cluster):
