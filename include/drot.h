@@ -92,8 +92,11 @@ typedef struct {
                                    runs); 0 (default): FP64 atomic adds into the totals (faster; the
                                    summation order, hence the last bits, may vary between runs) */
     int autotune;               /* 1: on the first solve of each (m, n), time the fused-step variants and tile
-                                   widths on a scratch plan and keep the fastest (costs one m x ld FP32
-                                   scratch buffer and a few launches); explicit step_variant / tile_k win */
+                                   widths on a scratch plan and keep the fastest unless it beats the default
+                                   plan by less than 3 % (costs one m x ld FP32 scratch buffer and a few
+                                   launches); explicit step_variant / tile_k win.  drot_solve_batched: on a
+                                   cold start of a batch shape not tuned yet, time four tile policies on the
+                                   batch itself before X_0 is written and keep the fastest for that shape */
     int persistent;             /* 1: run the iterations in one cooperative launch (every CTA resident, two
                                    bounded grid barriers per iteration, register-fed step, FP64-atomic
                                    totals); 0: CUDA graphs of [step, finish] launches (default) */
