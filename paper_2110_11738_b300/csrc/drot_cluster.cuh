@@ -150,14 +150,28 @@ __global__ void __launch_bounds__(kClusterThreads, 1) drot_cluster_kernel(Cluste
             float* xr = S.Xs + (size_t)i * npad;
             const float* cr = S.Cs + (size_t)i * npad;
             float rs = 0.f;
-            for (long long j = lane; j < n; j += 32) {
-                const float d = fmaf(-rhof, cr[j], phi + S.psi[j]);
-                const float xn = fmaxf(xr[j] + d, 0.f);
-                xr[j] = xn;
-                rs += xn;
-                scx = fmaf(cr[j], xn, scx);
-                const float dp = fmaxf(d, 0.f);
-                sd = fmaf(dp, dp, sd);
+            // four consecutive columns per lane per pass, 16-byte shared-memory accesses (rows and
+            // psi start on 16-byte boundaries: npad is a multiple of 4); columns >= n are left alone
+            for (int j4 = lane * 4; j4 < n; j4 += 128) {
+                const float4 xv = *reinterpret_cast<const float4*>(xr + j4);
+                const float4 cv = *reinterpret_cast<const float4*>(cr + j4);
+                const float4 pv = *reinterpret_cast<const float4*>(S.psi + j4);
+                float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+                const float cs4[4] = {cv.x, cv.y, cv.z, cv.w};
+                const float ps4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (j4 + e < n) {
+                        const float d = fmaf(-rhof, cs4[e], phi + ps4[e]);
+                        const float xn = fmaxf(xs[e] + d, 0.f);
+                        xs[e] = xn;
+                        rs += xn;
+                        scx = fmaf(cs4[e], xn, scx);
+                        const float dp = fmaxf(d, 0.f);
+                        sd = fmaf(dp, dp, sd);
+                    }
+                }
+                *reinterpret_cast<float4*>(xr + j4) = make_float4(xs[0], xs[1], xs[2], xs[3]);
             }
             rs = warp_sum_f32(rs);
             if (lane == 0) S.u[i] = (double)rs;
