@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
     constexpr int KMAX = 4;
     __shared__ double s_col[kWarps][128 * KMAX];
     __shared__ double s_red[kWarps][2];
+    __shared__ float s_psi[128 * KMAX];  // psi of the segment's tile and phi of a chunk of its rows,
+    __shared__ float s_phi[kPhiChunk];   // formed once per CTA (FP64 is scarce: see step_body)
 
     wait_for_predecessor();
     const int lane = threadIdx.x & 31;
@@ -116,23 +118,38 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
         const double cs = P.sc->c;
         const float rho = UPDATE ? (float)P.sc->rho : 0.f;
 
-        float psi[KMAX][4], cacc[KMAX][4];
-#pragma unroll
-        for (int kk = 0; kk < KMAX; ++kk)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const long long j = col0 + kk * 128 + lane * 4 + e;
-                psi[kk][e] = (UPDATE && kk < K && j < n) ? (float)((P.h[j] + cs) * P.inv_m) : 0.f;
-                cacc[kk][e] = 0.f;
+        // every thread arrives here together (the previous segment ended with a barrier)
+        if (UPDATE) {
+            for (int x = threadIdx.x; x < TW; x += kThreads) {
+                const long long j = col0 + x;
+                s_psi[x] = j < n ? (float)((P.h[j] + cs) * P.inv_m) : 0.f;
             }
+        }
+        float psi[KMAX][4], cacc[KMAX][4];
         for (int x = lane; x < TW; x += 32) s_col[warp][x] = 0.0;
-        __syncwarp();
 
         float scx = 0.f, sd = 0.f;
         double scx64 = 0.0, sd64 = 0.0;
         int since_flush = 0;
-        for (long long i = i0 + warp; i < i1; i += kWarps) {
-            const float phi = UPDATE ? (float)((P.g[i] + cs) * P.inv_n) : 0.f;
+        for (long long r0 = i0; r0 < i1; r0 += kPhiChunk) {  // kPhiChunk is a multiple of kWarps
+        const long long r1 = min(i1, r0 + (long long)kPhiChunk);
+        if (UPDATE) {
+            if (r0 != i0) __syncthreads();  // every warp is done with the previous chunk's phi
+            for (long long r = r0 + threadIdx.x; r < r1; r += kThreads)
+                s_phi[r - r0] = (float)((P.g[r] + cs) * P.inv_n);
+        }
+        __syncthreads();
+        if (r0 == i0) {
+#pragma unroll
+            for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    psi[kk][e] = (UPDATE && kk < K) ? s_psi[kk * 128 + lane * 4 + e] : 0.f;
+                    cacc[kk][e] = 0.f;
+                }
+        }
+        for (long long i = r0 + warp; i < r1; i += kWarps) {
+            const float phi = UPDATE ? s_phi[i - r0] : 0.f;
             const long long rowoff = i * ld + col0 + lane * 4;
             float4 xv[KMAX], cv[KMAX];
 #pragma unroll
@@ -196,6 +213,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
                 since_flush = 0;
             }
         }
+        }  // row chunks
 #pragma unroll
         for (int kk = 0; kk < KMAX; ++kk)
 #pragma unroll

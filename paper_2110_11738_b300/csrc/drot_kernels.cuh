@@ -40,7 +40,8 @@ namespace drot {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kFlushRows = 16;  // rows per warp between FP32 -> FP64 promotions
+constexpr int kFlushRows = 16;   // rows per warp between FP32 -> FP64 promotions
+constexpr int kPhiChunk = 4096;  // rows whose phi a CTA forms at once (a multiple of kWarps)
 // Finish blocks are small so that the O(m + n) FP64 work (B300's FP64 rate is a
 // small fraction of its FP32 rate) spreads over every SM.
 constexpr int kFinishThreads = 64;
@@ -187,6 +188,12 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
     constexpr int TW = 128 * K;
     __shared__ double s_col[kWarps][TW];
     __shared__ double s_red[kWarps][2];
+    // psi of the tile's columns and phi of a chunk of rows, formed once per CTA: a warp
+    // would otherwise compute its own copy of all of them in FP64, whose throughput on
+    // this GPU (a warp-wide FP64 instruction holds a sub-partition's pipe ~80 cycles)
+    // made the per-warp copies a burst of ~5 us at every tile start
+    __shared__ float s_psi[TW];
+    __shared__ float s_phi[kPhiChunk];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -205,23 +212,39 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
         const long long i0 = w - t * m, i1 = seg_end - t * m;
         const long long col0 = t * TW;
 
-        float psi[K][4], cacc[K][4];
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const long long j = col0 + kk * 128 + lane * 4 + e;
-                psi[kk][e] = (UPDATE && j < n) ? (float)((__ldcg(A.h + j) + cs) * A.inv_m) : 0.f;
-                cacc[kk][e] = 0.f;
+        // every thread arrives here together (the previous segment ended with a barrier)
+        if (UPDATE) {
+            for (int x = threadIdx.x; x < TW; x += kThreads) {
+                const long long j = col0 + x;
+                s_psi[x] = j < n ? (float)((__ldcg(A.h + j) + cs) * A.inv_m) : 0.f;
             }
         }
+        float psi[K][4], cacc[K][4];
         for (int x = lane; x < TW; x += 32) s_col[warp][x] = 0.0;
-        __syncwarp();
 
         float scx = 0.f, sd = 0.f;
         int since_flush = 0;
-        for (long long i = i0 + warp; i < i1; i += kWarps) {
-            const float phi = UPDATE ? (float)((__ldcg(A.g + i) + cs) * A.inv_n) : 0.f;
+        // rows in chunks of kPhiChunk (a multiple of kWarps, so warp w keeps the rows
+        // i0 + w + kWarps j of the whole segment, in the same order)
+        for (long long r0 = i0; r0 < i1; r0 += kPhiChunk) {
+        const long long r1 = min(i1, r0 + (long long)kPhiChunk);
+        if (UPDATE) {
+            if (r0 != i0) __syncthreads();  // every warp is done with the previous chunk's phi
+            for (long long r = r0 + threadIdx.x; r < r1; r += kThreads)
+                s_phi[r - r0] = (float)((__ldcg(A.g + r) + cs) * A.inv_n);
+        }
+        __syncthreads();
+        if (r0 == i0) {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    psi[kk][e] = UPDATE ? s_psi[kk * 128 + lane * 4 + e] : 0.f;
+                    cacc[kk][e] = 0.f;
+                }
+        }
+        for (long long i = r0 + warp; i < r1; i += kWarps) {
+            const float phi = UPDATE ? s_phi[i - r0] : 0.f;
             const long long rowoff = i * ld + col0 + lane * 4;
             float4 xv[K], cv[K];
 #pragma unroll
@@ -290,6 +313,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
                 since_flush = 0;
             }
         }
+        }  // row chunks
 #pragma unroll
         for (int kk = 0; kk < K; ++kk)
 #pragma unroll
