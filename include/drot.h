@@ -66,7 +66,8 @@ typedef enum {
     DROT_ERR_OOM = 3,           /* device or pinned-host allocation failed */
     DROT_ERR_CUDA = 4,          /* a CUDA runtime call failed (message via drot_last_error) */
     DROT_NOT_CONVERGED = 5,     /* max_iter iterations ran; outputs hold the last iterate */
-    DROT_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits */
+    DROT_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up (persistent grid barrier, TMA ring);
+                                   the context stays usable */
     DROT_ERR_NONFINITE = 7,     /* a NaN/Inf appeared in the iteration; outputs hold the last iterate */
     DROT_ERR_TOO_LARGE = 8      /* drot_solve_static: the problem's workspace exceeds DROT_STATIC_SCRATCH_BYTES */
 } drot_status;
