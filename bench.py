@@ -258,7 +258,8 @@ def run_ours(args):
     rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
     solver = drot.Solver(device=local, profile=False, stop_rule=rule, step_variant=args.step_variant,
                          tile_k=args.tile_k, autotune=not args.no_autotune and not args.persistent,
-                         deterministic=args.deterministic, persistent=args.persistent, c_skip=args.c_skip)
+                         deterministic=args.deterministic, persistent=args.persistent, c_skip=args.c_skip,
+                         serpentine=args.serpentine)
 
     def one_solve():
         return solver.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
@@ -299,7 +300,7 @@ def run_ours(args):
     # this pass runs without programmatic dependent launch; the kernels are the same).
     psolver = drot.Solver(device=local, profile=True, stop_rule=rule, step_variant=prof["step_variant"],
                           tile_k=prof["tile_k"], deterministic=args.deterministic, persistent=args.persistent,
-                          c_skip=args.c_skip)
+                          c_skip=args.c_skip, serpentine=args.serpentine)
     psolver.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)  # warm-up
     psolver.reset_profile()
     barrier()
@@ -368,7 +369,8 @@ def run_ours(args):
                    "sums": "fixed-order partials" if args.deterministic else "FP64 atomics",
                    "plan": "autotuned" if not args.no_autotune and not args.persistent else "default",
                    "iteration": "persistent cooperative launch" if args.persistent else "CUDA graphs",
-                   "c_skip": bool(args.c_skip)},
+                   "c_skip": bool(args.c_skip),
+                   "pass_order": "forward" if args.serpentine < 0 else "serpentine"},
         "iters_to_tol": iters,
         "status": statuses,
         "ms_per_iter": ms_per_solve / statistics.mean(iters),
@@ -418,6 +420,8 @@ def main(argv=None):
     ap.add_argument("--deterministic", action="store_true", help="fixed-order partial sums instead of atomics")
     ap.add_argument("--step-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="fused step: 1 register-fed, 2 TMA-fed, 3 async-copy-fed, 0 library default")
+    ap.add_argument("--serpentine", type=int, default=0, choices=[-1, 0, 1],
+                    help="pass order of the register-fed step: 1 alternate, -1 forward only, 0 library default")
     ap.add_argument("--max-iter", type=int, default=3_000_000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample-iters", type=int, default=8)

@@ -124,6 +124,12 @@ typedef struct {
                                    that makes every other CTA leave, and the solve returns
                                    DROT_ERR_TIMEOUT with the context intact.  A small value makes the
                                    barriers give up at once: it exists to test that path */
+    int serpentine;             /* order of the FP32 fused-step passes: 1 alternate (every other pass walks
+                                   each CTA's rows backwards, so it starts on the lines of X and C the pass
+                                   before it left in L2; the automatic graph length is then even), -1 every
+                                   pass forwards, 0 automatic (alternate).  Changes only the order in which
+                                   partial sums are formed, hence the last bits of a run.  The FP64 and
+                                   batched solves always walk forwards */
 } drot_config;
 
 typedef struct {

@@ -457,6 +457,9 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
         const double t_iter = 12.0 * (double)m * (double)n / 6.0e12 + 6.0e-6;
         gi = (int)std::lround(2.0e-3 / t_iter);
         gi = std::max(1, std::min(gi, 256));
+        // serpentine passes alternate by their position in the replay: an even count
+        // keeps the alternation across replay boundaries
+        if (h->cfg.serpentine >= 0) gi = std::max(2, gi + (gi & 1));
     }
     if (h->cfg.c_skip) gi = std::max(2, gi + (gi & 1));  // whole (C-reading, C-free) pairs per replay
     P.graph_iters = gi;
@@ -527,6 +530,8 @@ drot::StepArgs step_args(const drot_handle *h, const Plan &P, long long m, long 
     A.v = h->v;
     A.acc = h->acc;
     A.accumulate = P.accumulate;
+    A.serp = h->cfg.serpentine >= 0 ? 1 : 0;
+    A.odd = 0;  // set per launch by the launcher
     A.C = C;
     A.X = X;
     A.g = h->g;
@@ -653,10 +658,12 @@ drot_status build_graphs(drot_handle *h, const GraphKey &key, const Plan &P, con
             const bool cskip = key.c_skip != 0;
             if (prof) err = cudaEventRecordWithFlags(h->ev[inst][3 * it], h->stream, cudaEventRecordExternal);
             const bool pdl = !prof;  // an event record between kernels would break the programmatic edge
+            drot::StepArgs Ai = A;
+            Ai.odd = it & 1;  // odd positions walk backwards when A.serp is set
             if (err == cudaSuccess)
                 err = A64     ? launch_step64<true>(P, *A64, h->stream, pdl)
-                      : cskip ? launch_step_cskip(P, A, (it & 1) ? 2 : 1, h->stream, pdl)
-                              : launch_step<true>(P, A, h->stream, pdl);
+                      : cskip ? launch_step_cskip(P, Ai, (it & 1) ? 2 : 1, h->stream, pdl)
+                              : launch_step<true>(P, Ai, h->stream, pdl);
             if (prof && err == cudaSuccess)
                 err = cudaEventRecordWithFlags(h->ev[inst][3 * it + 1], h->stream, cudaEventRecordExternal);
             if (err == cudaSuccess) {
@@ -711,10 +718,16 @@ drot_status autotune_shape(drot_handle *h, long long m, long long n, long long l
             if (out != DROT_OK) break;
             DROT_CUDA(h, cudaMemsetAsync(h->g, 0, sizeof(double) * m, h->stream));
             DROT_CUDA(h, cudaMemsetAsync(h->h, 0, sizeof(double) * n, h->stream));
-            const drot::StepArgs A = step_args(h, P, m, n, ld, C, Xs);
+            // alternating directions, as the solve runs them (the warm-up pass is odd, so
+            // the first timed pass follows a backward one)
+            drot::StepArgs A = step_args(h, P, m, n, ld, C, Xs);
+            A.odd = 1;
             DROT_CUDA(h, launch_step<true>(P, A, h->stream));
             DROT_CUDA(h, cudaEventRecord(e0, h->stream));
-            for (int r = 0; r < 6; ++r) DROT_CUDA(h, launch_step<true>(P, A, h->stream));
+            for (int r = 0; r < 6; ++r) {
+                A.odd = r & 1;
+                DROT_CUDA(h, launch_step<true>(P, A, h->stream));
+            }
             DROT_CUDA(h, cudaEventRecord(e1, h->stream));
             DROT_CUDA(h, cudaEventSynchronize(e1));
             h->prof.kernel_launches += 7;
@@ -1840,6 +1853,7 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
     A.rowpart = rowpart; A.colpart = colpart; A.ctapart = ctapart;
     A.wbound = d_wbound; A.slot_base = d_slot_base;
     A.m = m; A.n = n; A.ld = ld; A.inv_n = 1.0 / (double)n; A.inv_m = 1.0 / (double)m;
+    A.serp = 1;  // serpentine passes (the default order of drot_solve)
     drot::FinishArgs F{};
     F.rowpart = rowpart; F.colpart = colpart; F.ctapart = ctapart; F.tile_slot = d_tile_slot;
     F.p = p; F.q = q; F.a = a_vec; F.b = b_vec; F.g = g_num; F.h = h_num; F.finpart = finpart; F.sc = sc;
@@ -1864,6 +1878,7 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
         const long long max_chunks = (max_iter + chunk - 1) / chunk + 1;
         for (long long c = 0; c < max_chunks && done == drot::kRunning; ++c) {
             for (long long it = 0; it < chunk; ++it) {
+                A.odd = (int)((c * chunk + it) & 1);
                 STATIC_CUDA(launch_step<true>(P, A, stream));
                 drot::drot_finish_kernel<<<fin_blocks, drot::kFinishThreads, 0, stream>>>(F);
                 STATIC_CUDA(cudaGetLastError());

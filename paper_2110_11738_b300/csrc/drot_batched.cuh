@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
     __shared__ double s_col[kWarps][128 * KMAX];
     __shared__ double s_red[kWarps][2];
     __shared__ float s_psi[128 * KMAX];  // psi of the segment's tile and phi of a chunk of its rows,
-    __shared__ float s_phi[kPhiChunk];   // formed once per CTA (FP64 is scarce: see step_body)
+    __shared__ float s_phi[kPhiChunk];   // formed once per CTA (FP64 is scarce: see StepSmem)
 
     wait_for_predecessor();
     const int lane = threadIdx.x & 31;

@@ -27,7 +27,9 @@
 // Segments are numbered tile-major (w = t*m + i) and each CTA takes one
 // contiguous range of segments whose boundaries the host balances by bytes.  Inside
 // a CTA the 8 warps take interleaved rows, so at any time a CTA streams 8
-// neighbouring row segments of X and C with 128-bit coalesced loads.  Row sums
+// neighbouring row segments of X and C with 128-bit coalesced loads.  Consecutive
+// passes walk the ranges in opposite directions (SegWalk), so that each pass starts on
+// what the previous one left in L2.  Row sums
 // are reduced with warp shuffles and written once per segment (rowpart[t][i]);
 // column sums accumulate in registers, are promoted to FP64 in shared memory every
 // few rows, reduced across warps and written once per (CTA, tile) ("slot").
@@ -89,6 +91,8 @@ struct StepArgs {
     double* v;                  // accumulation mode: column totals (n)
     double* acc;                // accumulation mode: [8] <C,X>, sum [d]_+^2 (added here), finish totals
     int accumulate;             // 1: atomics into u, v, acc; 0: fixed-order partials
+    int serp;                   // 1: alternate the direction of the passes (see SegWalk)
+    int odd;                    // parity of this pass in its launch sequence; backwards when serp && odd
     const long long* wbound;    // [G+1] segment range of each CTA
     const int* slot_base;       // [G]   first slot of each CTA
     long long m, n, ld;
@@ -177,23 +181,63 @@ __device__ __forceinline__ float4 ld_stream_ro(const float* p) {
     return __ldg(reinterpret_cast<const float4*>(p));
 }
 
+// The row segments of one CTA, [w0, w1) in tile-major numbering, walked forwards or
+// backwards.  Serpentine order: a pass that walks backwards (tiles, and rows within a
+// tile, in reverse) starts on the lines of X and C that the forward pass before it
+// touched last, which are still in L2 when the plan is a few times larger than L2.
+// Forwards, the k-th row of a segment visited is i0 + k; backwards it is i1 - 1 - k,
+// and warp w takes the k = w + kWarps j in both cases.  Column-partial slots keep
+// their tile: a backward walk starts at the CTA's last slot.
+struct SegWalk {
+    long long w0, w1, m;
+    bool rev;
+    __device__ __forceinline__ long long start() const { return rev ? w1 : w0; }
+    __device__ __forceinline__ bool more(long long w) const { return rev ? w > w0 : w < w1; }
+    // tile t and rows [i0, i1) of the segment at position w of the walk
+    __device__ __forceinline__ void seg(long long w, long long& t, long long& i0, long long& i1) const {
+        t = (rev ? w - 1 : w) / m;
+        const long long lo = rev ? max(w0, t * m) : w;
+        const long long hi = rev ? w : min(w1, (t + 1) * m);
+        i0 = lo - t * m;
+        i1 = hi - t * m;
+    }
+    __device__ __forceinline__ long long next(long long t, long long i0, long long i1) const {
+        return t * m + (rev ? i0 : i1);
+    }
+    __device__ __forceinline__ int first_slot(int base) const {
+        return base + ((rev && w1 > w0) ? (int)((w1 - 1) / m - w0 / m) : 0);
+    }
+    __device__ __forceinline__ long long row(long long i0, long long i1, long long k) const {
+        return rev ? i1 - 1 - k : i0 + k;
+    }
+};
+
 // The fused DR pass (UPDATE = true) or a plain row/column-sum pass over X
 // (UPDATE = false, used once to initialise a_0 and b_0 from the stored X_0).
 // C-load skipping (Claim 1, Sec. 3.3): CM = 0 is the plain pass; CM = 1 reads X and C
 // and stores W = x+ - rho c instead of x+; CM = 2 reads W (no C) and forms
 // x+ = [W + phi + psi]_+.  A CM = 1 / CM = 2 pair moves 12 + 8 bytes per entry;
 // <C,X> and the dual residual need C and are only produced by CM = 0 / 1 passes.
-template <int K, bool UPDATE, int CM = 0>
-__device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
-    constexpr int TW = 128 * K;
-    __shared__ double s_col[kWarps][TW];
-    __shared__ double s_red[kWarps][2];
+// Shared memory of the register-fed pass, declared by the kernel that runs it.
+template <int K>
+struct StepSmem {
+    double col[kWarps][128 * K];
+    double red[kWarps][2];
     // psi of the tile's columns and phi of a chunk of rows, formed once per CTA: a warp
     // would otherwise compute its own copy of all of them in FP64, whose throughput on
     // this GPU (a warp-wide FP64 instruction holds a sub-partition's pipe ~80 cycles)
     // made the per-warp copies a burst of ~5 us at every tile start
-    __shared__ float s_psi[TW];
-    __shared__ float s_phi[kPhiChunk];
+    float psi[128 * K];
+    float phi[kPhiChunk];
+};
+
+template <int K, bool UPDATE, int CM>
+__device__ __forceinline__ void step_pass(const StepArgs& A, int cta, StepSmem<K>& sm, const bool rev) {
+    constexpr int TW = 128 * K;
+    auto& s_col = sm.col;
+    auto& s_red = sm.red;
+    float* s_psi = sm.psi;
+    float* s_phi = sm.phi;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -202,14 +246,13 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
     const long long w1 = A.wbound[cta + 1];
     const float rho = UPDATE ? (float)A.sc->rho : 0.f;
     const double cs = __ldcg(&A.sc->c);
-    int slot = A.slot_base[cta];
+    const SegWalk walk{w0, w1, m, rev};
+    int slot = walk.first_slot(A.slot_base[cta]);
     double scx64 = 0.0, sd64 = 0.0;
 
-    long long w = w0;
-    while (w < w1) {
-        const long long t = w / m;
-        const long long seg_end = min(w1, (t + 1) * m);
-        const long long i0 = w - t * m, i1 = seg_end - t * m;
+    for (long long w = walk.start(); walk.more(w);) {
+        long long t, i0, i1;
+        walk.seg(w, t, i0, i1);
         const long long col0 = t * TW;
 
         // every thread arrives here together (the previous segment ended with a barrier)
@@ -225,16 +268,19 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
         float scx = 0.f, sd = 0.f;
         int since_flush = 0;
         // rows in chunks of kPhiChunk (a multiple of kWarps, so warp w keeps the rows
-        // i0 + w + kWarps j of the whole segment, in the same order)
-        for (long long r0 = i0; r0 < i1; r0 += kPhiChunk) {
-        const long long r1 = min(i1, r0 + (long long)kPhiChunk);
+        // k = w + kWarps j of the whole segment, in the same order); the chunk edge c
+        // is the chunk's first row forwards and one past its last row backwards
+        const long long c_first = rev ? i1 : i0;
+        for (long long c = c_first; rev ? c > i0 : c < i1; c += rev ? -kPhiChunk : kPhiChunk) {
+        const long long r0 = rev ? max(i0, c - (long long)kPhiChunk) : c;
+        const long long r1 = rev ? c : min(i1, c + (long long)kPhiChunk);
         if (UPDATE) {
-            if (r0 != i0) __syncthreads();  // every warp is done with the previous chunk's phi
+            if (c != c_first) __syncthreads();  // every warp is done with the previous chunk's phi
             for (long long r = r0 + threadIdx.x; r < r1; r += kThreads)
                 s_phi[r - r0] = (float)((__ldcg(A.g + r) + cs) * A.inv_n);
         }
         __syncthreads();
-        if (r0 == i0) {
+        if (c == c_first) {
 #pragma unroll
             for (int kk = 0; kk < K; ++kk)
 #pragma unroll
@@ -243,7 +289,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
                     cacc[kk][e] = 0.f;
                 }
         }
-        for (long long i = r0 + warp; i < r1; i += kWarps) {
+        for (long long i = rev ? r1 - 1 - warp : r0 + warp; rev ? i >= r0 : i < r1; i += rev ? -kWarps : kWarps) {
             const float phi = UPDATE ? s_phi[i - r0] : 0.f;
             const long long rowoff = i * ld + col0 + lane * 4;
             float4 xv[K], cv[K];
@@ -330,8 +376,8 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
             else if (col0 + x < n) atomicAdd(A.v + col0 + x, v);
         }
         __syncthreads();
-        ++slot;
-        w = seg_end;
+        slot += rev ? -1 : 1;
+        w = walk.next(t, i0, i1);
     }
 
     if (UPDATE) {
@@ -350,10 +396,16 @@ __device__ __forceinline__ void step_body(const StepArgs& A, int cta) {
 }
 
 template <int K, bool UPDATE, int CM = 0>
+__device__ __forceinline__ void step_body(const StepArgs& A, int cta, bool rev) {
+    __shared__ StepSmem<K> sm;
+    step_pass<K, UPDATE, CM>(A, cta, sm, rev);
+}
+
+template <int K, bool UPDATE, int CM = 0>
 __global__ void __launch_bounds__(kThreads, 2) drot_step_kernel(StepArgs A) {
     wait_for_predecessor();
     if (A.sc->done != kRunning) return;
-    step_body<K, UPDATE, CM>(A, blockIdx.x);
+    step_body<K, UPDATE, CM>(A, blockIdx.x, A.serp != 0 && A.odd != 0);
 }
 
 // X = W + rho C: restores the plan after a solve that stopped on a C-reading pass of
@@ -474,6 +526,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
     const long long m = A.m, n = A.n, ld = A.ld;
     const long long w0 = A.wbound[blockIdx.x];
     const long long w1 = A.wbound[blockIdx.x + 1];
+    const SegWalk walk{w0, w1, m, A.serp != 0 && A.odd != 0};
     if (threadIdx.x == 0) {
         for (int st = 0; st < S; ++st) {
             mbar_init(&full[st], 1);
@@ -492,29 +545,29 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
         // ---------------- producer: one lane issues every bulk copy
         if (lane == 0) {
             uint32_t g = 0;
-            for (long long w = w0; w < w1 && ok;) {
-                const long long t = w / m;
-                const long long seg_end = min(w1, (t + 1) * m);
-                const long long i0 = w - t * m, i1 = seg_end - t * m;
+            for (long long w = walk.start(); walk.more(w) && ok;) {
+                long long t, i0, i1;
+                walk.seg(w, t, i0, i1);
                 const long long col0 = t * TW;
                 const long long cols = min((long long)TW, n - col0);
                 const uint32_t bytes = (uint32_t)(((cols + 3) / 4) * 16);
-                for (long long r0 = i0; r0 < i1; r0 += R, ++g) {
+                // stage g holds the segment's rows k0 .. k0 + R - 1 in walk order
+                for (long long k0 = 0; k0 < i1 - i0; k0 += R, ++g) {
                     const int st = (int)(g % S);
                     const uint32_t use = g / S;
                     if (!mbar_wait(&empty[st], (use & 1u) ^ 1u, &s_abort)) {
                         ok = false;
                         break;
                     }
-                    const int rows = (int)min((long long)R, i1 - r0);
+                    const int rows = (int)min((long long)R, i1 - i0 - k0);
                     mbar_arrive_expect_tx(&full[st], (uint32_t)rows * 2u * bytes);
                     for (int rr = 0; rr < rows; ++rr) {
-                        const long long off = (r0 + rr) * ld + col0;
+                        const long long off = walk.row(i0, i1, k0 + rr) * ld + col0;
                         bulk_load(sX + ((size_t)st * R + rr) * TW, A.X + off, bytes, &full[st]);
                         bulk_load(sC + ((size_t)st * R + rr) * TW, A.C + off, bytes, &full[st]);
                     }
                 }
-                w = seg_end;
+                w = walk.next(t, i0, i1);
             }
             s_issued = g;
             if (!ok) {
@@ -527,12 +580,11 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
         // ---------------- consumers
         const double cs = A.sc->c;
         const float rho = (float)A.sc->rho;
-        int slot = A.slot_base[blockIdx.x];
+        int slot = walk.first_slot(A.slot_base[blockIdx.x]);
         uint32_t g = 0;
-        for (long long w = w0; w < w1;) {
-            const long long t = w / m;
-            const long long seg_end = min(w1, (t + 1) * m);
-            const long long i0 = w - t * m, i1 = seg_end - t * m;
+        for (long long w = walk.start(); walk.more(w);) {
+            long long t, i0, i1;
+            walk.seg(w, t, i0, i1);
             const long long col0 = t * TW;
 
             float psi[K][4], cacc[K][4];
@@ -549,7 +601,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
 
             float scx = 0.f, sd = 0.f;
             int since_flush = 0;
-            for (long long r0 = i0; r0 < i1; r0 += R, ++g) {
+            for (long long k0 = 0; k0 < i1 - i0; k0 += R, ++g) {
                 const int st = (int)(g % S);
                 const uint32_t use = g / S;
                 if (ok && !mbar_wait(&full[st], use & 1u, &s_abort)) {
@@ -559,8 +611,8 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
                         atomicExch(const_cast<int*>(&A.sc->fault), 1);
                     }
                 }
-                const long long i = r0 + warp;
-                if (ok && i < i1) {
+                const long long i = walk.row(i0, i1, k0 + warp);
+                if (ok && k0 + warp < i1 - i0) {
                     const float phi = (float)((A.g[i] + cs) * A.inv_n);
                     const float* xs_row = sX + ((size_t)st * R + warp) * TW;
                     const float* cs_row = sC + ((size_t)st * R + warp) * TW;
@@ -636,8 +688,8 @@ __global__ void __launch_bounds__(kThreads + 32, 1) drot_step_tma_kernel(StepArg
                 else if (col0 + x < n) atomicAdd(A.v + col0 + x, v);
             }
             consumer_sync();
-            ++slot;
-            w = seg_end;
+            slot += walk.rev ? -1 : 1;
+            w = walk.next(t, i0, i1);
         }
     }
 
@@ -690,15 +742,15 @@ struct AsyncLayout {
                                         : (size_t)kWarps * TW * sizeof(double);
 };
 
-// Copies row r of this warp's rows in the tile (row first + kWarps r, if r < nr) of X
-// and C into ring stage r mod S, and commits a group (empty past the last row, which
-// keeps the group count in step).
+// Copies row r of this warp's rows in the tile (row first + stride r, if r < nr; the
+// stride is kWarps forwards, -kWarps backwards) of X and C into ring stage r mod S, and
+// commits a group (empty past the last row, which keeps the group count in step).
 template <int K, int S>
-__device__ __forceinline__ void async_issue_row(const StepArgs& A, float* ring, long long first, int nr,
-                                                long long col0, int lane, int r) {
+__device__ __forceinline__ void async_issue_row(const StepArgs& A, float* ring, long long first, long long stride,
+                                                int nr, long long col0, int lane, int r) {
     constexpr int TW = 128 * K;
     if (r < nr) {
-        const long long i = first + (long long)kWarps * r;
+        const long long i = first + stride * r;
         float* xs = ring + (size_t)(r % S) * 2 * TW;
         float* cs_ = xs + TW;
         const long long rowoff = i * A.ld + col0 + lane * 4;
@@ -726,6 +778,8 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
     const long long m = A.m, n = A.n, ld = A.ld;
     const long long w0 = A.wbound[blockIdx.x];
     const long long w1 = A.wbound[blockIdx.x + 1];
+    const SegWalk walk{w0, w1, m, A.serp != 0 && A.odd != 0};
+    const long long stride = walk.rev ? -kWarps : kWarps;
 
     // The copies of the first S - 1 rows go out before the wait for the preceding
     // finish kernel: X and C are final once that kernel runs (it waited for the step
@@ -733,12 +787,12 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
     // accumulated only after the wait.  A solve that has already stopped skips them.
     bool primed = false;
     if (w0 < w1 && __ldcg(&A.sc->done) == kRunning) {
-        const long long t = w0 / m;
-        const long long i0 = w0 - t * m, i1 = min(w1, (t + 1) * m) - t * m;
-        const long long first = i0 + warp;
-        const int nr = first < i1 ? (int)((i1 - 1 - first) / kWarps + 1) : 0;
+        long long t, i0, i1;
+        walk.seg(walk.start(), t, i0, i1);
+        const long long first = walk.row(i0, i1, warp);
+        const int nr = warp < i1 - i0 ? (int)((i1 - i0 - 1 - warp) / kWarps + 1) : 0;
 #pragma unroll
-        for (int r = 0; r < S - 1; ++r) async_issue_row<K, S>(A, ring, first, nr, t * TW, lane, r);
+        for (int r = 0; r < S - 1; ++r) async_issue_row<K, S>(A, ring, first, stride, nr, t * TW, lane, r);
         primed = true;
     }
     wait_for_predecessor();
@@ -749,14 +803,12 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
 
     const float rho = (float)A.sc->rho;
     const double cs = A.sc->c;
-    int slot = A.slot_base[blockIdx.x];
+    int slot = walk.first_slot(A.slot_base[blockIdx.x]);
     double scx64 = 0.0, sd64 = 0.0;
 
-    long long w = w0;
-    while (w < w1) {
-        const long long t = w / m;
-        const long long seg_end = min(w1, (t + 1) * m);
-        const long long i0 = w - t * m, i1 = seg_end - t * m;
+    for (long long w = walk.start(); walk.more(w);) {
+        long long t, i0, i1;
+        walk.seg(w, t, i0, i1);
         const long long col0 = t * TW;
 
         float psi[K][4], cacc[K][4];
@@ -770,10 +822,11 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
                 cacc[kk][e] = 0.f;
                 cacc64[kk][e] = 0.0;
             }
-        // rows of this warp in the tile: i0 + warp + kWarps * r, r = 0 .. nr-1
-        const long long first = i0 + warp;
-        const int nr = first < i1 ? (int)((i1 - 1 - first) / kWarps + 1) : 0;
-        auto issue = [&](int r) { async_issue_row<K, S>(A, ring, first, nr, col0, lane, r); };
+        // rows of this warp in the tile: the segment's rows k = warp + kWarps r in walk
+        // order, r = 0 .. nr-1
+        const long long first = walk.row(i0, i1, warp);
+        const int nr = warp < i1 - i0 ? (int)((i1 - i0 - 1 - warp) / kWarps + 1) : 0;
+        auto issue = [&](int r) { async_issue_row<K, S>(A, ring, first, stride, nr, col0, lane, r); };
         if (!primed) {
 #pragma unroll
             for (int r = 0; r < S - 1; ++r) issue(r);
@@ -785,7 +838,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
         for (int r = 0; r < nr; ++r) {
             issue(r + S - 1);
             cp_async_wait<S - 1>();
-            const long long i = first + (long long)kWarps * r;
+            const long long i = first + stride * r;
             const float* xs = ring + (size_t)(r % S) * 2 * TW;
             const float* csr = xs + TW;
             const float phi = (float)((A.g[i] + cs) * A.inv_n);
@@ -864,8 +917,8 @@ __global__ void __launch_bounds__(kThreads, 2) drot_step_async_kernel(StepArgs A
             else if (col0 + x < n) atomicAdd(A.v + col0 + x, v);
         }
         __syncthreads();
-        ++slot;
-        w = seg_end;
+        slot += walk.rev ? -1 : 1;
+        w = walk.next(t, i0, i1);
     }
 
     double v[2] = {scx64, sd64};
@@ -1258,11 +1311,12 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, Scalars* sc) {
 template <int K>
 __global__ void __launch_bounds__(kThreads, 2) drot_persistent_kernel(StepArgs A, FinishArgs F, GridSync* gs,
                                                                       long long budget) {
+    __shared__ StepSmem<K> sm;
     Scalars* sc = F.sc;
     for (long long it = 0; it < budget; ++it) {
         if (*(volatile int*)&sc->done != kRunning) break;  // uniform: read after a barrier
         const unsigned long long t0 = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
-        step_body<K, true>(A, blockIdx.x);
+        step_pass<K, true, 0>(A, blockIdx.x, sm, A.serp != 0 && (it & 1) != 0);
         if (!grid_barrier(gs, sc)) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             gs->step_ns += global_ns() - t0;

@@ -91,9 +91,50 @@ def test_step_parity_every_variant_and_tile_width(variant, tile_k, grid):
         assert s.profile()["step_variant"] == variant and s.profile()["tile_k"] == tile_k
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("tile_k", [1, 4])
+@pytest.mark.parametrize("k", [2, 5])
+def test_forward_only_order_keeps_parity(variant, tile_k, k):
+    """serpentine=-1: every pass walks forwards; the default alternates (odd passes
+    walk each CTA's rows backwards).  Both are the same iteration in another order of
+    the partial sums."""
+    pr = workloads.make_problem("plain_256", seed=6, m=211, n=1100)
+    with drot.Solver(device=0, tile_k=tile_k, grid_ctas=29, step_variant=variant, serpentine=-1) as s:
+        _step_parity(s, pr, k, seed=10)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_serpentine_first_pass_is_forward_and_orders_agree(variant):
+    pr = workloads.make_problem("plain_8192x6144", seed=17, m=333, n=1500)
+    X0, mu0, nu0 = workloads.random_start(pr.m, pr.n, seed=3)
+    res = {}
+    for serp in (1, -1):
+        for k in (1, 40):
+            C, p, q, X, mu, nu = _gpu_inputs(pr, X0, mu0, nu0)
+            with drot.Solver(device=0, deterministic=True, step_variant=variant, grid_ctas=41,
+                             serpentine=serp) as s:
+                s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=k, X=X, mu=mu, nu=nu, warm=True)
+            res[serp, k] = (X.cpu().numpy(), mu.cpu().numpy())
+    # one pass: both orders walk forwards, bit for bit the same
+    assert np.array_equal(res[1, 1][0], res[-1, 1][0]) and np.array_equal(res[1, 1][1], res[-1, 1][1])
+    # forty passes: the orders differ only in the rounding of the partial sums
+    S = max(np.abs(X0).max(), pr.rho * (np.abs(mu0).max() + np.abs(nu0).max() + 1.0))
+    assert np.abs(res[1, 40][0].astype(np.float64) - res[-1, 40][0]).max() <= 8 * EPS32 * S * 40
+    assert np.abs(res[1, 40][1] - res[-1, 40][1]).max() <= 64 * EPS32 * S / pr.rho * 40
+
+
+def test_serpentine_with_an_odd_replay_length():
+    """An odd graph length puts two passes of one direction back to back at every replay
+    boundary: only the order changes, the iterates still follow the oracle."""
+    pr = workloads.make_problem("plain_256", seed=8, m=150, n=700)
+    with drot.Solver(device=0, graph_iters=3, grid_ctas=23) as s:
+        _step_parity(s, pr, 7, seed=12)
+
+
 def test_variants_agree_bitwise_on_a_solve():
-    # the two fused-step variants perform the same FP32 operations in the same order
-    # per entry and write the same partials, so whole runs agree bit for bit
+    # the three fused-step variants perform the same FP32 operations in the same order
+    # per entry, walk the rows in the same (serpentine) order and write the same
+    # partials, so whole runs agree bit for bit
     pr = workloads.make_problem("plain_8192x6144", seed=12, m=517, n=1029)
     outs = {}
     for v in (1, 2, 3):
