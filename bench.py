@@ -555,7 +555,7 @@ def run_batched(args):
 
     probs = device_batch()
     rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
-    solver = drot.Solver(device=local, stop_rule=rule, autotune=not args.no_autotune)
+    solver = drot.Solver(device=local, stop_rule=rule, autotune=not args.no_autotune, serpentine=args.serpentine)
     for _ in range(args.warmup):
         solver.solve_batched(probs, tol=args.tol, max_iter=args.max_iter, check=False)
     sampler = ClockSampler(local)
@@ -595,7 +595,8 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched_512", "B": len(specs), "m_n_range": [64, 2048], "seed": args.seed,
                    "tiles": "autotuned" if not args.no_autotune else "default",
-                   "tol": args.tol, "stop_rule": args.stop, "total_entries": int(sum(pr.m * pr.n for pr in specs))},
+                   "tol": args.tol, "stop_rule": args.stop, "total_entries": int(sum(pr.m * pr.n for pr in specs)),
+                   "pass_order": "forward" if args.serpentine < 0 else "serpentine"},
         "iters_to_tol": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
         "status": sorted({r["status_name"] for r in res}),
         "gpu_launches": int(prof["kernel_launches"]),

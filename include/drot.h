@@ -128,8 +128,8 @@ typedef struct {
                                    each CTA's rows backwards, so it starts on the lines of X and C the pass
                                    before it left in L2; the automatic graph length is then even), -1 every
                                    pass forwards, 0 automatic (alternate).  Changes only the order in which
-                                   partial sums are formed, hence the last bits of a run.  The FP64 and
-                                   batched solves always walk forwards */
+                                   partial sums are formed, hence the last bits of a run.  Also applies
+                                   to drot_solve_batched; the FP64 solve always walks forwards */
 } drot_config;
 
 typedef struct {

@@ -1105,7 +1105,7 @@ void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector
 
 struct BatchDev {
     drot::BatchProb *probs;
-    int *active, *nactive, *fin_prob, *fin_local, *flags;
+    int *active, *nactive, *parity, *fin_prob, *fin_local, *flags;
     long long *unit0, *wbound;
 };
 
@@ -1207,6 +1207,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     D.unit0 = carve<long long>(cur, B + 1);
     D.wbound = carve<long long>(cur, G + 1);
     D.nactive = carve<int>(cur, 1);
+    D.parity = carve<int>(cur, 1);
 
     // scalar state of every problem, then the marginal checks
     std::vector<Scalars> hs(B);
@@ -1221,6 +1222,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     }
     DROT_CUDA(h, cudaMemcpyAsync(d_sc, hs.data(), sizeof(Scalars) * B, cudaMemcpyHostToDevice, h->stream));
     DROT_CUDA(h, cudaMemsetAsync(base + align_up(sizeof(Scalars) * B, 256), 0, vec_bytes, h->stream));
+    DROT_CUDA(h, cudaMemsetAsync(D.parity, 0, sizeof(int), h->stream));
     DROT_CUDA(h, cudaMemcpyAsync(D.probs, hp.data(), sizeof(drot::BatchProb) * B, cudaMemcpyHostToDevice, h->stream));
     drot::drot_batched_vector_sums_kernel<<<B, 1024, 0, h->stream>>>(D.probs, warm);
     DROT_CUDA(h, cudaGetLastError());
@@ -1247,7 +1249,10 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     A.fin_prob = D.fin_prob;
     A.fin_local = D.fin_local;
     A.nactive = D.nactive;
+    A.parity = D.parity;
     A.warm = warm;
+    A.serp = h->cfg.serpentine >= 0 ? 1 : 0;
+    A.odd = 0;
 
     // Tile policy autotuning (autotune = 1, cold starts, a batch shape not tuned yet):
     // time the fused step of this batch under every candidate policy, one warm-up and
@@ -1276,10 +1281,14 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
             build_batch_lists(hp, valid, G, FB, TL);
             tst = upload_lists(h, TL, D, FB);
             if (tst != DROT_OK) break;
-            drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(A);
+            // alternating directions, as the solve runs them
+            drot::BatchArgs At = A;
+            At.odd = 1;
+            drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(At);
             e = cudaEventRecord(e0, h->stream);
             for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-                drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(A);
+                At.odd = r & 1;
+                drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(At);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
@@ -1359,7 +1368,9 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         DROT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t err = cudaSuccess;
         for (int it = 0; it < g && err == cudaSuccess; ++it) {
-            err = launch_k(drot::drot_batched_step_kernel<true>, dim3(G), dim3(drot::kThreads), 0, h->stream, true, A);
+            drot::BatchArgs Ai = A;
+            Ai.odd = it & 1;  // added to the parity word the host keeps between replays
+            err = launch_k(drot::drot_batched_step_kernel<true>, dim3(G), dim3(drot::kThreads), 0, h->stream, true, Ai);
             if (err == cudaSuccess)
                 err = launch_k(drot::drot_batched_finish_kernel, dim3(FB), dim3(drot::kBatchFinishThreads), 0, h->stream,
                                true, A);
@@ -1382,6 +1393,8 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     if (max_iter > 0 && nvalid > 0) {
         std::vector<int> active = valid;
         const long long max_replays = max_iter + 2;  // every replay advances every active problem
+        long long iters_run = 0;  // iterations every active problem has run so far
+        int dev_parity = 0;       // the device's parity word
         for (long long r = 0; r < max_replays && !active.empty(); ++r) {
             const int gi = pick_gi(active);
             cudaGraphExec_t exec = nullptr;
@@ -1390,7 +1403,14 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
                 release();
                 return st;
             }
-            cudaError_t e = cudaGraphLaunch(exec, h->stream);
+            cudaError_t e = cudaSuccess;
+            const int want = (int)(iters_run & 1);
+            if (want != dev_parity) {  // after a replay of odd length (pageable source: staged before return)
+                e = cudaMemcpyAsync(D.parity, &want, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+                dev_parity = want;
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, h->stream);
+            iters_run += gi;
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(h->h_bstat, d_sc, sizeof(Scalars) * B, cudaMemcpyDeviceToHost, h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -49,7 +49,10 @@ struct BatchArgs {
     const int* fin_prob;       // [FB] problem served by each finish block (-1: idle)
     const int* fin_local;      // [FB] index of the block within its problem's group
     const int* nactive;        // number of active problems (device, updated between replays)
+    const int* parity;         // parity of the iterations already run (device, updated between replays)
     int warm;
+    int serp;                  // 1: alternate the direction of the passes (as SegWalk does)
+    int odd;                   // parity of this pass in its graph; backwards when serp and parity + odd is odd
 };
 
 __device__ __forceinline__ FinishArgs batch_finish_args(const BatchProb& P) {
@@ -91,25 +94,35 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
     const long long w1 = B.wbound[blockIdx.x + 1];
     const int nactive = *B.nactive;
     if (w0 >= w1 || nactive <= 0) return;
+    // Serpentine order (see SegWalk): every active problem has run the same number of
+    // iterations, so one parity serves the whole launch.  Backwards, the problems, the
+    // tiles of a problem and the rows of a tile are all walked in reverse.
+    const bool rev = B.serp != 0 && ((*B.parity + B.odd) & 1) != 0;
 
-    // the active problem holding w0: the last a with unit0[a] <= w0
+    // the active problem holding the first segment walked: the last a with unit0[a] <= it
+    const long long wfirst = rev ? w1 - 1 : w0;
     int lo = 0, hi = nactive - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (B.unit0[mid] <= w0) lo = mid;
+        if (B.unit0[mid] <= wfirst) lo = mid;
         else hi = mid - 1;
     }
     int ai = lo;
-    long long w = w0;
-    while (w < w1) {
-        while (ai + 1 < nactive && w >= B.unit0[ai + 1]) ++ai;
+    long long w = rev ? w1 : w0;
+    while (rev ? w > w0 : w < w1) {
+        if (rev) {
+            while (ai > 0 && w - 1 < B.unit0[ai]) --ai;
+        } else {
+            while (ai + 1 < nactive && w >= B.unit0[ai + 1]) ++ai;
+        }
         const BatchProb& P = B.probs[B.active[ai]];
         const long long base = B.unit0[ai];
         const long long m = P.m, n = P.n, ld = P.ld;
-        const long long t = (w - base) / m;
-        const long long seg_end = min(w1, base + (t + 1) * m);
-        const long long i0 = w - base - t * m, i1 = seg_end - base - t * m;
-        w = seg_end;
+        const long long t = ((rev ? w - 1 : w) - base) / m;
+        const long long seg_lo = rev ? max(w0, base + t * m) : w;
+        const long long seg_hi = rev ? w : min(w1, base + (t + 1) * m);
+        const long long i0 = seg_lo - base - t * m, i1 = seg_hi - base - t * m;
+        w = rev ? seg_lo : seg_hi;
         if (P.sc->done != kRunning) continue;  // uniform: every thread reads the same flag
 
         const int K = P.K;
@@ -131,15 +144,19 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
         float scx = 0.f, sd = 0.f;
         double scx64 = 0.0, sd64 = 0.0;
         int since_flush = 0;
-        for (long long r0 = i0; r0 < i1; r0 += kPhiChunk) {  // kPhiChunk is a multiple of kWarps
-        const long long r1 = min(i1, r0 + (long long)kPhiChunk);
+        // chunks of kPhiChunk rows (a multiple of kWarps); the chunk edge c is the chunk's
+        // first row forwards and one past its last row backwards
+        const long long c_first = rev ? i1 : i0;
+        for (long long c = c_first; rev ? c > i0 : c < i1; c += rev ? -kPhiChunk : kPhiChunk) {
+        const long long r0 = rev ? max(i0, c - (long long)kPhiChunk) : c;
+        const long long r1 = rev ? c : min(i1, c + (long long)kPhiChunk);
         if (UPDATE) {
-            if (r0 != i0) __syncthreads();  // every warp is done with the previous chunk's phi
+            if (c != c_first) __syncthreads();  // every warp is done with the previous chunk's phi
             for (long long r = r0 + threadIdx.x; r < r1; r += kThreads)
                 s_phi[r - r0] = (float)((P.g[r] + cs) * P.inv_n);
         }
         __syncthreads();
-        if (r0 == i0) {
+        if (c == c_first) {
 #pragma unroll
             for (int kk = 0; kk < KMAX; ++kk)
 #pragma unroll
@@ -148,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
                     cacc[kk][e] = 0.f;
                 }
         }
-        for (long long i = r0 + warp; i < r1; i += kWarps) {
+        for (long long i = rev ? r1 - 1 - warp : r0 + warp; rev ? i >= r0 : i < r1; i += rev ? -kWarps : kWarps) {
             const float phi = UPDATE ? s_phi[i - r0] : 0.f;
             const long long rowoff = i * ld + col0 + lane * 4;
             float4 xv[KMAX], cv[KMAX];

@@ -35,7 +35,11 @@ def _shapes():
     return [(1, 1), (3, 7), (64, 2048), (517, 63), (200, 1029), (1000, 130), (33, 4100), (257, 257)]
 
 
-def test_batched_step_parity_with_oracle():
+# default: alternating pass directions within each graph; graph_iters=1: one iteration per
+# replay, so the direction comes from the parity word the host rewrites between replays;
+# serpentine=-1: every pass forwards
+@pytest.mark.parametrize("cfg", [{}, {"graph_iters": 1}, {"serpentine": -1}])
+def test_batched_step_parity_with_oracle(cfg):
     probs, starts, specs = [], [], []
     for b, (m, n) in enumerate(_shapes()):
         pr = workloads.make_problem("plain_8192x6144", seed=100 + b, m=m, n=n)
@@ -43,7 +47,7 @@ def test_batched_step_parity_with_oracle():
         probs.append(_dev_problem(pr, X0, mu0, nu0))
         starts.append((X0, mu0, nu0))
         specs.append(pr)
-    with drot.Solver(device=0) as s:
+    with drot.Solver(device=0, **cfg) as s:
         res = s.solve_batched(probs, tol=-1.0, max_iter=3, warm=True)
     for pr, P, (X0, mu0, nu0), r in zip(specs, probs, starts, res):
         assert r["status"] == drot.DROT_NOT_CONVERGED and r["iters"] == 3
