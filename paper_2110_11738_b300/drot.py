@@ -172,7 +172,9 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
                 cluster: int = 0, trace=None, wait_limit: int = 0, serpentine: int = 0) -> int:
     """Create a solver handle; returns the opaque handle as an int.  ``trace``: optional float64
     CUDA tensor of 2 * L entries that receives <C, X_k> and the l1 residual of iterations 1 .. L
-    of every solve (the caller keeps it alive while the handle is used)."""
+    of every solve (the caller keeps it alive while the handle is used).  ``serpentine``: 1 or 0
+    (default) alternates the direction of the fused-step passes so that each starts on what the
+    previous one left in L2; -1 runs every pass forwards."""
     lib = load()
     cfg = DrotConfig()
     lib.drot_config_default(ctypes.byref(cfg))
