@@ -36,9 +36,10 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 def test_status_strings_without_gpu():
     lib = drot.load()
-    for code in range(8):
+    for code in range(9):  # DROT_OK .. DROT_ERR_TOO_LARGE
         assert lib.drot_status_string(code)
     assert lib.drot_status_string(5) == b"iteration cap reached"
+    assert b"static workspace" in lib.drot_status_string(drot.DROT_ERR_TOO_LARGE)
 
 
 def test_ctypes_layouts_match_c(tmp_path):
@@ -65,3 +66,41 @@ def test_create_without_device_fails_cleanly():
     st = lib.drot_create(ctypes.byref(h), None)
     assert st == drot.DROT_ERR_CUDA and not h.value
     assert lib.drot_destroy(None) == 0
+
+
+def _static_call(lib, m, n, ld, C=16, p=8, q=8, X=16, mu=8, nu=8, tol=1e-6, max_iter=10):
+    # The pointer values are never dereferenced: every case below is refused by the host-side
+    # checks before the library asks the driver for the current device.
+    return lib.drot_solve_static(m, n, C, ld, p, q, 0.0, tol, max_iter, X, mu, nu, 0, None, None)
+
+
+@pytest.mark.parametrize("case", [
+    dict(m=0, n=4, ld=4),                   # empty: no source points
+    dict(m=4, n=0, ld=4),                   # empty: no target points
+    dict(m=-3, n=4, ld=4),
+    dict(m=4, n=5, ld=4),                   # pitch shorter than a row
+    dict(m=4, n=5, ld=6),                   # pitch not a multiple of 4 floats (16-byte rows)
+    dict(m=4, n=4, ld=4, C=0),              # NULL buffers
+    dict(m=4, n=4, ld=4, nu=0),
+    dict(m=4, n=4, ld=4, X=24),             # X not 16-byte aligned
+    dict(m=4, n=4, ld=4, p=12),             # p not 8-byte aligned
+    dict(m=4, n=4, ld=4, max_iter=-1),
+    dict(m=4, n=4, ld=4, tol=float("nan")),
+    dict(m=1 << 30, n=1 << 12, ld=1 << 12),  # m * n beyond 2^40 entries
+])
+def test_static_solve_rejects_bad_arguments_without_touching_the_device(case):
+    lib = drot.load()
+    assert _static_call(lib, **case) == drot.DROT_ERR_INVALID_ARG
+
+
+def test_handle_calls_reject_a_null_handle():
+    lib = drot.load()
+    res = drot.DrotResult()
+    assert lib.drot_solve(None, 4, 4, 16, 4, 8, 8, 0.0, 1e-6, 10, 16, 8, 8, 0, ctypes.byref(res)) == \
+        drot.DROT_ERR_INVALID_ARG
+    assert lib.drot_solve_f64(None, 4, 4, 16, 4, 8, 8, 0.0, 1e-6, 10, 16, 8, 8, 0, ctypes.byref(res)) == \
+        drot.DROT_ERR_INVALID_ARG
+    assert lib.drot_solve_batched(None, 1, None, 1e-6, 10, 0, None) == drot.DROT_ERR_INVALID_ARG
+    assert lib.drot_get_profile(None, ctypes.byref(drot.DrotProfile())) == drot.DROT_ERR_INVALID_ARG
+    assert lib.drot_reset_profile(None) == drot.DROT_ERR_INVALID_ARG
+    assert lib.drot_last_error(None) == b""
