@@ -18,6 +18,9 @@ Contents
   {X : X e = p, X^T f = q}.
 * :func:`lp_optimum`, :func:`permutation_optimum`, :func:`nw_corner_1d` -
   exact optima from an LP library, brute force and the 1-D closed form.
+* :func:`lp_primal_dual`, :func:`fixed_point_from_pair` - an exact
+  primal-dual optimum from the LP library and the DR fixed point it defines
+  (Lemma opt-rel, Appendix A.2), the Y* of Theorem 1 (Sec. 3.2).
 * :func:`plan_stats` - the Sec. 3.1 stopping quantities of any (X, mu, nu).
 """
 
@@ -222,6 +225,38 @@ def lp_optimum(C, p, q):
     if res.status != 0:
         raise RuntimeError(f"HiGHS failed: {res.message}")
     return float(res.fun), res.x.reshape(m, n)
+
+
+def lp_primal_dual(C, p, q):
+    """Exact primal-dual optimum (X*, mu*, nu*, value) of eq. ot:dist via HiGHS.
+
+    mu*, nu* are the multipliers of the row and column constraints (HiGHS reports the
+    sensitivity of the optimal value to the right-hand side), i.e. a solution of the dual
+    max p^T mu + q^T nu s.t. mu_i + nu_j <= C_ij.  Callers check dual feasibility and strong
+    duality themselves before using them.
+    """
+    from scipy.optimize import linprog
+
+    C = np.asarray(C, dtype=np.float64)
+    m, n = C.shape
+    rows = np.zeros((m, m * n))
+    for i in range(m):
+        rows[i, i * n:(i + 1) * n] = 1.0
+    cols = np.zeros((n, m * n))
+    for j in range(n):
+        cols[j, j::n] = 1.0
+    res = linprog(C.ravel(), A_eq=np.vstack([rows, cols]), b_eq=np.concatenate([p, q]), bounds=(0, None),
+                  method="highs")
+    if res.status != 0:
+        raise RuntimeError(f"HiGHS failed: {res.message}")
+    y = np.asarray(res.eqlin.marginals, dtype=np.float64)
+    return res.x.reshape(m, n), y[:m].copy(), y[m:].copy(), float(res.fun)
+
+
+def fixed_point_from_pair(X, mu, nu, rho):
+    """Lemma opt-rel (Appendix A.2): a primal-dual optimum (X*, mu*, nu*) gives the fixed
+    point Y* = X* + rho (mu* e^T + f nu*^T) of the DR operator T of eq. dr:operator:T."""
+    return np.asarray(X, dtype=np.float64) + rho * (np.asarray(mu)[:, None] + np.asarray(nu)[None, :])
 
 
 def permutation_optimum(C):

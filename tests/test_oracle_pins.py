@@ -4,6 +4,9 @@
   itself checked against a generic least-squares projection;
 * the identities of Appendix A.2 (Lemma var:repr) and the a_k recursion (Sec. 3.1);
 * firm nonexpansiveness of the DR operator (Appendix A): ||Y_{k+1} - Y_k|| non-increasing;
+* Theorem 1 (Sec. 3.2): distance to a fixed point Y* (built from an LP primal-dual optimum by
+  Lemma opt-rel) non-increasing, the O(1/k) bound on the ergodic objective, the identity
+  ||Zbar_k - Xbar_k|| = ||Y_k - Y_0|| / k with Z_k from Lemma 1's projection, and its 2||Y_0 - Y*||/k bound;
 * exact optima: brute force over permutations (Birkhoff-von Neumann), the 1-D
   monotone (north-west-corner) plan, and an LP solver (HiGHS);
 * Prop. 1 at convergence.
@@ -109,6 +112,59 @@ def test_lemma_var_repr_identities_and_nonexpansiveness():
         prev_step = step
 
 
+# ------------------------------------------------------------- Theorem 1 (Sec. 3.2)
+
+def _theorem1_violations(C, p, q, rho, iters):
+    """Run Algorithm 1 (the C oracle) from X_0 = p q^T and check Theorem 1's statements at
+    every k; return the names of those that fail (an empty list when all hold).
+
+    Y* is the fixed point Lemma opt-rel builds from an exact LP primal-dual optimum, and
+    Z_{k+1} = P(2 X_{k+1} - Y_k) comes from Lemma 1's projection, independently of the
+    oracle's own update of Y."""
+    m, n = C.shape
+    Xs, mus, nus, opt = oracle.lp_primal_dual(C, p, q)
+    # the LP pair must be an exact optimum before it can define Y*
+    assert (mus[:, None] + nus[None, :] - C).max() <= 1e-12
+    assert abs(p @ mus + q @ nus - opt) <= 1e-12 and abs((C * Xs).sum() - opt) <= 1e-12
+    Ystar = oracle.fixed_point_from_pair(Xs, mus, nus, rho)
+    # T(Y*) = Y*: one step of the three-variable form from Y* returns it
+    _, _, Ys = oracle.dr3_run(C, p, q, rho, 1, Ystar)
+    assert np.abs(Ys[1] - Ystar).max() <= 1e-12
+
+    st = oracle.StepState(C, p, q, rho, np.outer(p, q), np.zeros(m), np.zeros(n))
+    Y0 = st.Y.copy()
+    d0 = np.linalg.norm(Y0 - Ystar)
+    const = np.linalg.norm(Y0) ** 2 / (2 * rho) + 2 / rho * np.linalg.norm(Xs) * d0
+    bad = set()
+    prev, sum_cx = d0, 0.0
+    sum_X, sum_Z = np.zeros_like(C), np.zeros_like(C)
+    for k in range(1, iters + 1):
+        Yk = st.Y.copy()
+        st.step()
+        X = st.X.copy()
+        sum_cx += (C * X).sum()
+        sum_X += X
+        sum_Z += oracle.project_marginals(2 * X - Yk, p, q)
+        d = np.linalg.norm(st.Y - Ystar)
+        if d > prev * (1 + 1e-12) + 1e-15:  # Fejer monotone: ||Y_k - Y*|| non-increasing
+            bad.add("fejer")
+        prev = d
+        if sum_cx / k - opt > const / k * (1 + 1e-12):  # <C, Xbar_k> - <C, X*> <= const / k
+            bad.add("objective")
+        feas = np.linalg.norm(sum_Z / k - sum_X / k)
+        if abs(feas - np.linalg.norm(st.Y - Y0) / k) > 1e-12 * max(1.0, feas):
+            bad.add("ergodic_identity")
+        if feas > 2 * d0 / k * (1 + 1e-12):
+            bad.add("feasibility")
+    return sorted(bad)
+
+
+@pytest.mark.parametrize("m,n,seed,marginals", [(9, 7, 12, "dirichlet"), (6, 6, 3, "uniform"), (12, 5, 4, "dirichlet")])
+def test_theorem1_sublinear_rate(m, n, seed, marginals):
+    C, p, q, rho, _ = _small(m, n, seed, marginals)
+    assert _theorem1_violations(C, p, q, rho, 300) == []
+
+
 # ----------------------------------------------------------------- exact optima
 
 @pytest.mark.parametrize("n,seed", [(3, 0), (5, 1), (6, 2), (7, 3)])
@@ -209,6 +265,8 @@ def _pin_battery():
         if abs(lhs - rhs) > 1e-9 * max(1, abs(rhs)):
             failed.append("var_repr")
             break
+    if _theorem1_violations(C, p, q, rho, 200):
+        failed.append("theorem1")
     opt, _ = oracle.lp_optimum(C, p, q)
     out = oracle.drot_solve(C, p, q, rho, tol=1e-9, max_iter=20000)
     if out["status"] != oracle.STATUS_CONVERGED or abs(out["stats"]["primal"] - opt) > 1e-7:
@@ -224,6 +282,18 @@ def test_pins_catch_planted_mistakes(mutation):
     finally:
         oracle.set_mutation(0)
     assert failed, f"mutation {mutation} slipped past every pin"
+
+
+@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 6, 7])
+def test_theorem1_pins_alone_catch_every_mistake_in_the_iteration(mutation):
+    # mutation 5 changes only the reported dual objective, not the iterates
+    C, p, q, rho, _ = _small(9, 7, 12)
+    try:
+        oracle.set_mutation(mutation)
+        failed = _theorem1_violations(C, p, q, rho, 300)
+    finally:
+        oracle.set_mutation(0)
+    assert failed, f"mutation {mutation} satisfies every statement of Theorem 1"
 
 
 def test_unmutated_oracle_passes_battery():
