@@ -139,3 +139,44 @@ def test_batched_autotuned_tiles_keep_parity():
         res_w = s.solve_batched(warm, tol=-1.0, max_iter=0, warm=True)
         for P, X0 in zip(warm, X_in):
             assert torch.equal(P["X"], X0)
+
+
+def test_full_512_problem_batch_in_the_benchmark_configuration():
+    """The whole 512-problem workload (m, n uniform in [64, 2048], seed 0), launched the way the
+    benchmark launches it: cold start, autotuned tile policy, duality-gap stopping rule, serpentine
+    passes.  Three iterations of every problem; then, for all 512, properties that hold at any size
+    (X >= 0, the reported <C, X> and l1 marginal residual equal an FP64 recomputation from the
+    returned plan), and for six sampled problems (the largest, the smallest, four seeded picks) the
+    plan, the duals and the objective against the FP64 oracle run from the same X_0 = p q^T
+    (rounded to FP32 as the GPU stores it)."""
+    k = 3
+    specs = workloads.make_batch(B=512, seed=0)
+    probs = [_dev_problem(pr) for pr in specs]
+    with drot.Solver(device=0, stop_rule=drot.STOP_GAP, autotune=True) as s:
+        res = s.solve_batched(probs, tol=-1.0, max_iter=k, check=False)
+    assert len(res) == 512
+    for pr, P, r in zip(specs, probs, res):
+        assert r["status"] == drot.DROT_NOT_CONVERGED and r["iters"] == k, (pr.name, r)
+        Xd = P["X"].to(torch.float64)
+        assert float(Xd.min()) >= 0.0
+        Cd = P["C"].to(torch.float64)
+        primal = float((Cd * Xd).sum())
+        res_l1 = float((Xd.sum(1) - P["p"]).abs().sum() + (Xd.sum(0) - P["q"]).abs().sum())
+        assert abs(primal - r["primal_obj"]) <= 1e-5 * abs(primal) + 1e-12, (pr.name, primal, r["primal_obj"])
+        assert abs(res_l1 - r["res_l1"]) <= 1e-5 * res_l1 + 1e-7, (pr.name, res_l1, r["res_l1"])
+    sizes = np.array([pr.m * pr.n for pr in specs])
+    picks = {int(sizes.argmax()), int(sizes.argmin())}
+    picks |= {int(b) for b in np.random.default_rng(1).choice(512, size=4, replace=False)}
+    for b in sorted(picks):
+        pr, P, r = specs[b], probs[b], res[b]
+        X0 = np.outer(pr.p, pr.q).astype(np.float32).astype(np.float64)
+        ref = oracle.drot_run(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, k, X0=X0, mu0=np.zeros(pr.m),
+                              nu0=np.zeros(pr.n))
+        S = max(np.abs(X0).max(), pr.rho, np.abs(ref["X"]).max())
+        Xg = P["X"].cpu().numpy().astype(np.float64)
+        assert np.abs(Xg - ref["X"]).max() <= 8 * EPS32 * S * k * 4, pr.name
+        assert np.abs(P["mu"].cpu().numpy() - ref["mu"]).max() <= 64 * EPS32 * S / pr.rho * k + 1e-12, pr.name
+        assert np.abs(P["nu"].cpu().numpy() - ref["nu"]).max() <= 64 * EPS32 * S / pr.rho * k + 1e-12, pr.name
+        h = ref["history"][-1]
+        assert abs(r["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9, pr.name
+        assert abs(r["res_l1"] - h[oracle.RES_L1]) <= 1e-5 * abs(h[oracle.RES_L1]) + 1e-7, pr.name

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import workloads
 from oracle import mlp as ref_mlp
 from paper_2110_11738_b300 import drot, warmstart
@@ -101,6 +102,42 @@ def test_seed_is_dual_feasible_and_tight():
     assert float(slack.min(dim=0).values.abs().max()) <= 1e-12  # every column tight
     assert np.array_equal(d["X"].cpu().numpy(), np.outer(pr.p, pr.q).astype(np.float32))
     net.close()
+
+
+def test_seeded_step_parity_full_size_1024():
+    """The seeded solve at the full 1024 x 1024 size of the warm-start workload (mixtures of four
+    Gaussians, Dirichlet marginals, a held-out seed): the network's c-transform seed enters as
+    (X_0 = p q^T, mu_0, nu_0) with phi_0 = rho mu_0 and psi_0 = rho nu_0 (Lemma opt-rel), and two
+    iterations of the warm-started solve, launched as the benchmark launches it, match the FP64
+    oracle run from the same seed: plan, duals, objective and l1 residual."""
+    k = 2
+    EPS32 = 2.0 ** -24
+    pr = workloads.make_problem("warm_1024", seed=20_000)
+    assert pr.m == 1024 and pr.n == 1024
+    net = drot.Mlp(0, workloads.mlp_init_params(7))
+    d = warmstart._device_problem(pr, 0)
+    xs = torch.as_tensor(pr.x, dtype=torch.float32, device="cuda").contiguous()
+    yt = torch.as_tensor(pr.y, dtype=torch.float32, device="cuda").contiguous()
+    net.warm_start(xs, yt, d["p"], d["q"], pr.cost_scale, d["C"], d["X"], d["mu"], d["nu"])
+    net.close()
+    X0 = d["X"].cpu().numpy().astype(np.float64)
+    mu0 = d["mu"].cpu().numpy().copy()
+    nu0 = d["nu"].cpu().numpy().copy()
+    with drot.Solver(device=0, stop_rule=drot.STOP_GAP) as s:
+        out = s.solve(d["C"], d["p"], d["q"], rho=pr.rho, tol=-1.0, max_iter=k, X=d["X"], mu=d["mu"], nu=d["nu"],
+                      warm=True)
+    assert out["status"] == drot.DROT_NOT_CONVERGED and out["iters"] == k
+    ref = oracle.drot_run(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, k, X0=X0, mu0=mu0, nu0=nu0)
+    S = max(np.abs(X0).max(), pr.rho * (np.abs(mu0).max() + np.abs(nu0).max() + 1.0), np.abs(ref["X"]).max())
+    Xg = d["X"].cpu().numpy().astype(np.float64)
+    assert Xg.min() >= 0.0
+    assert np.abs(Xg - ref["X"]).max() <= 8 * EPS32 * S * k * 4
+    tol_d = 64 * EPS32 * S / pr.rho * k + 1e-12
+    assert np.abs(d["mu"].cpu().numpy() - ref["mu"]).max() <= tol_d
+    assert np.abs(d["nu"].cpu().numpy() - ref["nu"]).max() <= tol_d
+    h = ref["history"][-1]
+    assert abs(out["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9
+    assert abs(out["res_l1"] - h[oracle.RES_L1]) <= 1e-5 * abs(h[oracle.RES_L1]) + 1e-7
 
 
 def _weighted_corr(a, b, w):
