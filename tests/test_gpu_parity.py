@@ -438,3 +438,33 @@ def test_nonfinite_cost_is_reported(solver):
                           check=False)
     assert out["status"] == drot.DROT_ERR_NONFINITE
     assert out["iters"] == 1
+
+
+@pytest.mark.parametrize("cfg", [{"cluster": 1}, {"cluster": 2}, "batched"])
+def test_resume_from_returned_state_retraces_the_run(cfg):
+    """Checkpoint and resume: the state an interrupted solve returns, (X_k, mu_k, nu_k), is a
+    complete checkpoint, because a warm start rebuilds a, b and alpha from their definitions
+    (a = Y e - p with Y = X + phi e^T + f psi^T, Sec. 3.1).  Three iterations, then three more
+    from the returned state, must match six uninterrupted iterations of the FP64 oracle."""
+    k1, k2 = 3, 3
+    pr = workloads.make_problem("plain_8192x6144", seed=41, m=130, n=257)
+    X0, mu0, nu0 = workloads.random_start(pr.m, pr.n, seed=42)
+    C, p, q, X, mu, nu = _gpu_inputs(pr, X0, mu0, nu0)
+    with drot.Solver(device=0, **({} if cfg == "batched" else cfg)) as s:
+        for k in (k1, k2):
+            if cfg == "batched":
+                out = s.solve_batched([dict(C=C, p=p, q=q, X=X, mu=mu, nu=nu, rho=pr.rho)], tol=-1.0, max_iter=k,
+                                      warm=True, check=False)[0]
+            else:
+                out = s.solve(C, p, q, rho=pr.rho, tol=-1.0, max_iter=k, X=X, mu=mu, nu=nu, warm=True, check=False)
+            assert out["status"] == drot.DROT_NOT_CONVERGED and out["iters"] == k
+    k = k1 + k2
+    ref = oracle.drot_run(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, k, X0=X0.astype(np.float64), mu0=mu0, nu0=nu0)
+    S = max(np.abs(X0).max(), pr.rho * (np.abs(mu0).max() + np.abs(nu0).max() + 1.0), np.abs(ref["X"]).max())
+    assert np.abs(X.cpu().numpy().astype(np.float64) - ref["X"]).max() <= 8 * EPS32 * S * k * 4
+    tol_d = 64 * EPS32 * S / pr.rho * k + 1e-12
+    assert np.abs(mu.cpu().numpy() - ref["mu"]).max() <= tol_d
+    assert np.abs(nu.cpu().numpy() - ref["nu"]).max() <= tol_d
+    h = ref["history"][-1]
+    assert abs(out["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9
+    assert abs(out["res_l1"] - h[oracle.RES_L1]) <= 1e-5 * abs(h[oracle.RES_L1]) + 1e-7
