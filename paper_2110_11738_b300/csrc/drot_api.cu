@@ -1541,7 +1541,14 @@ drot_status solve_entry(drot_handle *h, int64_t m, int64_t n, const T *C, int64_
         }
         st = solve_device(h, m, n, dC, ld, dp, dq, rho, tol, max_iter, dX, dmu, dnu, warm, res, f64);
         if (st == DROT_OK || st == DROT_NOT_CONVERGED || st == DROT_ERR_NONFINITE) {
-            DROT_CUDA(h, cudaMemcpyAsync(X, dX, mb, cudaMemcpyDeviceToHost, h->stream));
+            // columns 0..n-1 of every row only: the caller's row padding is never written (a cold
+            // start uploads no X, so the workspace's padding holds nothing of the caller's)
+            if (ld == n) {
+                DROT_CUDA(h, cudaMemcpyAsync(X, dX, mb, cudaMemcpyDeviceToHost, h->stream));
+            } else {
+                DROT_CUDA(h, cudaMemcpy2DAsync(X, sizeof(T) * ld, dX, sizeof(T) * ld, sizeof(T) * n, m,
+                                               cudaMemcpyDeviceToHost, h->stream));
+            }
             DROT_CUDA(h, cudaMemcpyAsync(mu, dmu, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
             DROT_CUDA(h, cudaMemcpyAsync(nu, dnu, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
             DROT_CUDA(h, cudaStreamSynchronize(h->stream));

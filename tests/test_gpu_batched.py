@@ -180,3 +180,34 @@ def test_full_512_problem_batch_in_the_benchmark_configuration():
         h = ref["history"][-1]
         assert abs(r["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9, pr.name
         assert abs(r["res_l1"] - h[oracle.RES_L1]) <= 1e-5 * abs(h[oracle.RES_L1]) + 1e-7, pr.name
+
+
+def test_batched_with_host_buffers_matches_the_oracle():
+    """drot_solve_batched on host (NumPy) buffers stages each problem through the device and
+    solves it with drot_solve's path; five cold-started iterations of each problem must match
+    the FP64 oracle from the same X_0 = p q^T (rounded to FP32)."""
+    k = 5
+    specs, probs = [], []
+    for b, (m, n) in enumerate([(3, 7), (130, 257), (64, 2048)]):
+        pr = workloads.make_problem("plain_8192x6144", seed=700 + b, m=m, n=n)
+        ld = workloads.pad_ld(n)
+        Ch = np.zeros((m, ld), np.float32)
+        Ch[:, :n] = pr.C
+        Xh = np.full((m, ld), 5.0, np.float32)  # a cold start overwrites the plan; the padding stays
+        probs.append(dict(C=Ch[:, :n], X=Xh[:, :n], p=pr.p.copy(), q=pr.q.copy(), mu=np.zeros(m), nu=np.zeros(n),
+                          rho=pr.rho, Xfull=Xh))
+        specs.append(pr)
+    with drot.Solver(device=0) as s:
+        res = drot.drot_solve_batched(s.handle, probs, tol=-1.0, max_iter=k, check=False)
+    for pr, P, r in zip(specs, probs, res):
+        assert r["status"] == drot.DROT_NOT_CONVERGED and r["iters"] == k
+        X0 = np.outer(pr.p, pr.q).astype(np.float32).astype(np.float64)
+        ref = oracle.drot_run(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, k, X0=X0, mu0=np.zeros(pr.m),
+                              nu0=np.zeros(pr.n))
+        S = max(np.abs(X0).max(), pr.rho, np.abs(ref["X"]).max())
+        assert np.abs(P["X"].astype(np.float64) - ref["X"]).max() <= 8 * EPS32 * S * k * 4
+        assert np.abs(P["mu"] - ref["mu"]).max() <= 64 * EPS32 * S / pr.rho * k + 1e-12
+        assert np.abs(P["nu"] - ref["nu"]).max() <= 64 * EPS32 * S / pr.rho * k + 1e-12
+        assert np.all(P["Xfull"][:, pr.n:] == 5.0)
+        h = ref["history"][-1]
+        assert abs(r["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9
