@@ -310,9 +310,10 @@ def test_golden_lp_optima_reached_by_oracle():
     cases = json.load(open(path))["cases"]
     for case in cases:
         pr = workloads.make_problem(case["config"], seed=case["seed"], m=case["m"], n=case["n"])
-        out = oracle.drot_solve(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, tol=1e-7, max_iter=600000,
+        # the Sec. 4 Gaussian case (48 x 48) needs about 1.6 million iterations at rho0 = 2
+        out = oracle.drot_solve(pr.C.astype(np.float64), pr.p, pr.q, pr.rho, tol=1e-10, max_iter=2_000_000,
                                 stop_on_dual_residual=False)
         assert out["status"] == oracle.STATUS_CONVERGED, case
-        assert abs(out["stats"]["primal"] - case["lp_optimum"]) < 1e-6, case
+        assert abs(out["stats"]["primal"] - case["lp_optimum"]) < 1e-7, case
         if "permutation_optimum" in case:
             assert abs(case["permutation_optimum"] - case["lp_optimum"]) < 1e-12
