@@ -38,8 +38,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "drot_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_LIB_OMP = os.path.join(_LIB_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 # Indices into the stats vector returned by the C oracle.
 PRIMAL, DUAL, GAP, RES_L1, RES_L2, DUAL_RES_PREV, BETA = range(7)
@@ -50,22 +51,35 @@ STATUS_MAX_ITER = 1
 STATUS_NONFINITE = 2
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle (plain -O2, IEEE semantics, single thread)."""
+def _compile(out: str, extra: list, force: bool) -> str:
     os.makedirs(_LIB_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
+def build(force: bool = False) -> str:
+    """Compile the C oracle twice: plain -O2 with IEEE semantics on one thread (the parity
+    reference), and the same source with -fopenmp (its row loops split across the host's
+    cores; used only to time the oracle on all cores)."""
+    _compile(_LIB_OMP, ["-fopenmp"], force)
+    return _compile(_LIB, [], force)
+
+
+def threads(all_cores: bool = True) -> int:
+    """Threads an iteration of the oracle uses: 1 for the parity build; the OpenMP runtime's
+    thread count (OMP_NUM_THREADS, else every host core) for the all-cores build."""
+    return int(_load(all_cores).oracle_threads())
+
+
+def _load(all_cores: bool = False):
+    key = bool(all_cores)
     with _lock:
-        if _lib is None:
+        if key not in _libs:
             build()
-            lib = ctypes.CDLL(_LIB)
+            lib = ctypes.CDLL(_LIB_OMP if key else _LIB)
             d = ctypes.POINTER(ctypes.c_double)
             i64 = ctypes.c_int64
             lib.oracle_solve.restype = ctypes.c_int
@@ -78,8 +92,10 @@ def _load():
             lib.oracle_init.argtypes = [i64, i64, d, d, d, d, d, d, d, d]
             lib.oracle_set_mutation.restype = None
             lib.oracle_set_mutation.argtypes = [ctypes.c_int]
-            _lib = lib
-    return _lib
+            lib.oracle_threads.restype = ctypes.c_int
+            lib.oracle_threads.argtypes = []
+            _libs[key] = lib
+    return _libs[key]
 
 
 def _ptr(a: np.ndarray):
@@ -132,10 +148,11 @@ def drot_run(C, p, q, rho, iters, X0=None, mu0=None, nu0=None):
 
 
 class StepState:
-    """Explicit Algorithm 1 state (X, phi, psi, a, b, alpha) stepped by the C oracle."""
+    """Explicit Algorithm 1 state (X, phi, psi, a, b, alpha) stepped by the C oracle
+    (``all_cores``: the OpenMP build of the same source, for timing on every host core)."""
 
-    def __init__(self, C, p, q, rho, X0, phi0, psi0):
-        self.lib = _load()
+    def __init__(self, C, p, q, rho, X0, phi0, psi0, all_cores: bool = False):
+        self.lib = _load(all_cores)
         self.C = np.ascontiguousarray(np.asarray(C, dtype=np.float64))
         self.p = np.ascontiguousarray(np.asarray(p, dtype=np.float64))
         self.q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))

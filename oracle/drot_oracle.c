@@ -39,11 +39,22 @@
  *
  * Mutations: oracle_set_mutation(k) plants one deliberate mistake (k > 0) so
  * the tests can show that their pins catch it.  k = 0 is the oracle proper.
+ *
+ * Threads: the same source is built twice.  Without OpenMP (the parity
+ * reference) the pragmas below are ignored and every loop runs in the order
+ * written.  With -fopenmp (used only to time the oracle on all host cores)
+ * the loops over rows, and the column-sum loop over columns, are split across
+ * threads; each r_i, s_j and X_ij is still formed by one thread in the order
+ * written, and only the three scalar totals (sum r, <C,X>, r_dual^2) are
+ * combined in an unspecified order.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* layout of the stats array filled by oracle_iterate / oracle_solve */
 enum {
@@ -61,6 +72,16 @@ static int g_mutation = 0;
 
 void oracle_set_mutation(int k) { g_mutation = k; }
 int oracle_nstats(void) { return ORC_NSTATS; }
+
+/* Threads the iteration uses (1 unless built with OpenMP). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* a_0, b_0, alpha_0 of Algorithm 1 for a start (X0, phi0, psi0). */
 void oracle_init(int64_t m, int64_t n, const double *p, const double *q,
@@ -98,6 +119,7 @@ void oracle_iterate(int64_t m, int64_t n, const double *C, const double *p, cons
 
     /* step 4, and ||[phi_k + psi_k - rho C]_+||_F^2 along the way */
     double dual_sq = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : dual_sq)
     for (int64_t i = 0; i < m; ++i) {
         for (int64_t j = 0; j < n; ++j) {
             double c = C[i * n + j];
@@ -111,12 +133,14 @@ void oracle_iterate(int64_t m, int64_t n, const double *C, const double *p, cons
 
     /* step 5: residuals of the new iterate and beta */
     double sum_r = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : sum_r)
     for (int64_t i = 0; i < m; ++i) {
         double row = 0.0;
         for (int64_t j = 0; j < n; ++j) row += X[i * n + j];
         r[i] = row - p[i];
         sum_r += r[i];
     }
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) {
         double col = 0.0;
         for (int64_t i = 0; i < m; ++i) col += X[i * n + j];
@@ -145,6 +169,7 @@ void oracle_iterate(int64_t m, int64_t n, const double *C, const double *p, cons
 
     /* stopping quantities at the new iterate */
     double primal = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : primal)
     for (int64_t i = 0; i < m; ++i)
         for (int64_t j = 0; j < n; ++j) primal += C[i * n + j] * X[i * n + j];
     double pphi = 0.0, qpsi = 0.0, l1 = 0.0, l2 = 0.0;
