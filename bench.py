@@ -5,9 +5,19 @@ from X_0 = p q^T until the stopping test fires at tol 1e-6.  By default the test
 is the metric's own condition, the duality gap of Sec. 3.1,
 |<C,X> - (p^T phi + q^T psi)/rho| <= 1e-6 (``--stop gap``); ``--stop full`` also
 requires ||X1 - p||_1 + ||X^T 1 - q||_1 <= 1e-6 (the library's default rule).  The
-l1 marginal residual at the stopping point is reported either way.  The default workload is the
-rectangular 8192 x 6144 problem (Gaussian clouds, random marginals, FP32 plan and
-cost, FP64 reductions).
+default workload is the largest single-GPU one, 20000 x 20000 (points uniform in
+[0,1]^3, uniform marginals, FP32 plan and cost, FP64 reductions).
+
+The gap alone can fall below 1e-6 long before the plan is feasible (primal and dual
+objectives cross), so the line also carries:
+  tolerance_met   which of gap <= tol and l1 residual <= tol hold at the stop;
+  final.certificate  FP64 bounds on the optimal value from the returned (X, mu, nu):
+                  a feasible plan's cost (X rounded onto the marginals) above it and a
+                  dual-feasible objective (the c-transform of mu) below it;
+  full_rule       one solve under the full test (gap and l1 residual <= tol) of the
+                  8192 x 6144 workload, with its time, iterations, status and certificate;
+  batched         one solve of the 512-problem batch (one problem per uneven shape)
+                  with the fraction of the HBM roofline over the whole solve.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -16,7 +26,8 @@ better); `roofline` reports the fused step kernel's algorithmic HBM traffic
 (12 bytes per plan entry per launch: read X, read C, write X) over its
 CUDA-event-timed launch duration; `e2e` is the same solve through the C ABI with
 host buffers (copies inside the timed region); `cpu_baseline` is the FP64 CPU
-oracle timed on a bounded sample of the same workload.
+oracle timed on a bounded sample of the same workload, on all host cores (OpenMP
+build) and on one core.
 
 Multi-GPU (torchrun): every rank solves its own replica of the problem (there
 is no exchange between independent solves), the max time over ranks is taken,
@@ -46,16 +57,17 @@ L2_BYTES = 126 * 1024 * 1024
 # oracle) arm to extrapolate its per-iteration time.  plain_256: the FP64 oracle's own
 # count (full rule: gap and l1 residual), run to completion on the CPU.  The larger
 # workloads cannot be run to completion by the oracle in a bench run; their counts are
-# those the FP32 GPU solver needed (the step-parity tests show both follow the same
-# iterates, and on plain_256 the counts agree to 0.5 %: 21535 vs 21434).
+# those the FP32 GPU solver needed ("GPU count, extrapolated" in the printed line; the
+# step-parity tests show both follow the same iterates, and on plain_256 the counts
+# agree to 0.5 %: 21535 vs 21434).
 ITERS_TO_TOL = {
-    ("plain_8192x6144", "gap"): 9526,
-    ("plain_256", "full"): 21434,
-    ("plain_256", "gap"): None,
-    ("plain_8192x6144", "full"): None,
-    ("plain_20000", "gap"): None,
-    ("plain_20000", "full"): None,
+    ("plain_20000", "gap"): (470, "GPU count, extrapolated"),
+    ("plain_8192x6144", "gap"): (9526, "GPU count, extrapolated"),
+    ("plain_256", "full"): (21434, "oracle's own count"),
 }
+
+DEFAULT_WORKLOAD = "plain_20000"
+FULL_RULE_WORKLOAD = "plain_8192x6144"
 
 
 def _peaks():
@@ -176,56 +188,253 @@ def _max_over_ranks(x, world, device):
     return float(t.item())
 
 
-def _cpu_baseline(workload, seed, iters_to_tol, sample_iters):
-    """The FP64 oracle as it stands, single-threaded, on `sample_iters` iterations of the full problem."""
+def _host_problem(workload, seed, pr=None):
+    """FP64 cost and marginals of the workload on the host (the oracle's inputs).  With ``pr``
+    (the problem already built on the GPU by the bit-identical torch builder) the FP32 cost is
+    copied back instead of being rebuilt."""
+    import numpy as np
+
+    import workloads
+
+    if pr is None:
+        pr = workloads.make_problem(workload, seed=seed)
+        C32 = pr.C
+    else:
+        C32 = pr.C[:, : pr.n].cpu().numpy()
+    return pr, np.ascontiguousarray(C32, dtype=np.float64)
+
+
+def _time_oracle_iterations(C, pr, iters, all_cores):
+    """Seconds per Algorithm-1 iteration of the FP64 oracle over `iters` iterations from
+    X_0 = p q^T, and the thread count it used."""
     import numpy as np
 
     import oracle
-    import workloads
 
-    pr = workloads.make_problem(workload, seed=seed)
-    C = pr.C.astype(np.float64)
-    st = oracle.StepState(C, pr.p, pr.q, pr.rho, np.outer(pr.p, pr.q), np.zeros(pr.m), np.zeros(pr.n))
+    st = oracle.StepState(C, pr.p, pr.q, pr.rho, np.outer(pr.p, pr.q), np.zeros(pr.m), np.zeros(pr.n),
+                          all_cores=all_cores)
     t0 = time.perf_counter()
-    for _ in range(sample_iters):
+    for _ in range(iters):
         st.step()
-    dt = time.perf_counter() - t0
-    per_iter = dt / sample_iters
-    return {
-        "value": per_iter * iters_to_tol if iters_to_tol else None,
-        "unit": "s",
-        "cores": 1,
-        "kind": "oracle",
-        "sample": (f"{sample_iters} Algorithm-1 iterations of the full {pr.m}x{pr.n} problem (FP64 C oracle, "
-                   f"{per_iter:.3f} s/iteration), extrapolated to {iters_to_tol} iterations to tol"),
-        "seconds_per_iteration": per_iter,
+    per_iter = (time.perf_counter() - t0) / iters
+    del st
+    return per_iter, oracle.threads(all_cores)
+
+
+def _cpu_baseline(workload, seed, iters_to_tol, count_kind, omp_iters, single_iters, pr=None):
+    """The FP64 oracle as it stands, timed on this host: on every core (its OpenMP build) and on
+    one core, each on a bounded sample of whole iterations of the full problem, extrapolated to
+    `iters_to_tol` iterations.  plain_256 is small enough for the oracle's own complete solve."""
+    import numpy as np
+
+    import oracle
+
+    if workload == "plain_256":
+        pr, C = _host_problem(workload, seed, None)
+        t0 = time.perf_counter()
+        out = oracle.drot_solve(C, pr.p, pr.q, pr.rho, tol=1e-6, max_iter=1_000_000)
+        secs = time.perf_counter() - t0
+        return {"value": secs, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": f"the oracle's complete solve to gap and l1 residual <= 1e-6 ({out['iters']} iterations, "
+                          f"FP64 C oracle, one core)"}
+    pr, C = _host_problem(workload, seed, pr)
+    omp_s, omp_threads = _time_oracle_iterations(C, pr, omp_iters, True)
+    one_s, _ = _time_oracle_iterations(C, pr, single_iters, False)
+    out = {
+        "value": omp_s * iters_to_tol, "unit": "s", "cores": omp_threads, "kind": "oracle",
+        "sample": (f"{omp_iters} Algorithm-1 iterations of the full {pr.m}x{pr.n} problem (FP64 C oracle, OpenMP "
+                   f"build on {omp_threads} threads of {os.cpu_count()} host cores, {omp_s:.3f} s/iteration), "
+                   f"extrapolated to {iters_to_tol} iterations to tol ({count_kind})"),
+        "seconds_per_iteration": omp_s, "nproc": os.cpu_count(),
+        "single_thread": {"value": one_s * iters_to_tol, "unit": "s", "cores": 1,
+                          "seconds_per_iteration": one_s,
+                          "sample": f"{single_iters} iterations on one core (the parity build), extrapolated the "
+                                    f"same way"},
     }
+    del C
+    return out
 
 
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    import oracle  # noqa: F401
+    import oracle
 
-    iters = ITERS_TO_TOL.get((args.workload, args.stop))
+    entry = ITERS_TO_TOL.get((args.workload, args.stop))
+    if entry is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no iteration count to extrapolate the oracle to for "
+                                                              f"{args.workload} under --stop {args.stop}"}))
+        return 0
+    iters, count_kind = entry
+    pr, C = _host_problem(args.workload, args.seed)
     t_steps = []
-    cb = None
-    for s in range(args.warmup + args.steps):
-        cb = _cpu_baseline(args.workload, args.seed, iters, args.sample_iters)
-        if s >= args.warmup:
-            t_steps.append(cb["value"] if cb["value"] is not None else float("nan"))
+    per_iter = []
+    if args.workload == "plain_256":
+        # small enough for the oracle's complete solve, every step
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            out = oracle.drot_solve(C, pr.p, pr.q, pr.rho, tol=args.tol, max_iter=1_000_000)
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                t_steps.append(dt)
+        sample = f"the oracle's complete solve ({out['iters']} iterations, one core), every step"
+        cores = 1
+    else:
+        import numpy as np
+
+        # one oracle state for the whole run: each step times the next iteration of the solve
+        st = oracle.StepState(C, pr.p, pr.q, pr.rho, np.outer(pr.p, pr.q), np.zeros(pr.m), np.zeros(pr.n),
+                              all_cores=True)
+        cores = oracle.threads(True)
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            st.step()
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                t_steps.append(dt * iters)
+                per_iter.append(dt)
+        sample = (f"each step: the next Algorithm-1 iteration of the full {pr.m}x{pr.n} problem (FP64 C oracle, OpenMP "
+                  f"build on {cores} threads of {os.cpu_count()} host cores, mean "
+                  f"{statistics.mean(per_iter):.3f} s/iteration), extrapolated to {iters} iterations ({count_kind})")
     value = statistics.mean(t_steps) if t_steps else None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": None if value is None else value * 1000.0,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "seed": args.seed, "tol": args.tol, "stop": args.stop},
-        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "config": {"workload": args.workload, "m": pr.m, "n": pr.n, "seed": args.seed, "tol": args.tol,
+                   "stop_rule": _rule_text(args.stop), "iterations_to_tol": iters, "iteration_count": count_kind},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _rule_text(stop):
+    return {"gap": "gap<=tol", "full": "gap<=tol and l1 residual<=tol"}[stop]
+
+
+def _certificate(C, p, q, X, mu, nu, block_rows=2048):
+    """Bounds on the optimal value of eq. ot:dist from a returned (X, mu, nu), in FP64.
+
+    upper: X rounded onto the transport polytope (rows scaled down to at most p_i, then columns
+           to at most q_j, the missing mass added as the rank-one plan e_r e_c^T / ||e_r||_1) is a
+           feasible plan, so its cost is >= the optimum;
+    lower: with the c-transform nu'_j = min_i (C_ij - mu_i), (mu, nu') is dual feasible, so
+           p^T mu + q^T nu' is <= the optimum (weak duality, eq. ot:dist:dual).
+    upper - lower bounds how far the rounded plan (and the dual) are from optimal.  Evaluation
+    only (outside every timed region): plain torch reductions over row blocks."""
+    import torch
+
+    m, n = X.shape
+    dev = X.device
+    p = p.to(torch.float64)
+    q = q.to(torch.float64)
+    rows = torch.zeros(m, dtype=torch.float64, device=dev)
+    cmin = torch.full((n,), float("inf"), dtype=torch.float64, device=dev)
+    primal = 0.0
+    for i0 in range(0, m, block_rows):
+        i1 = min(m, i0 + block_rows)
+        Xb = X[i0:i1].to(torch.float64)
+        Cb = C[i0:i1].to(torch.float64)
+        rows[i0:i1] = Xb.sum(1)
+        primal += float((Cb * Xb).sum())
+        cmin = torch.minimum(cmin, (Cb - mu[i0:i1, None]).min(0).values)
+    xs = torch.where(rows > p, p / rows, torch.ones_like(rows))
+    cols = torch.zeros(n, dtype=torch.float64, device=dev)
+    for i0 in range(0, m, block_rows):
+        i1 = min(m, i0 + block_rows)
+        cols += (X[i0:i1].to(torch.float64) * xs[i0:i1, None]).sum(0)
+    ys = torch.where(cols > q, q / cols, torch.ones_like(cols))
+    rows2 = torch.zeros(m, dtype=torch.float64, device=dev)
+    cost2 = 0.0
+    for i0 in range(0, m, block_rows):
+        i1 = min(m, i0 + block_rows)
+        Xb = X[i0:i1].to(torch.float64) * xs[i0:i1, None] * ys[None, :]
+        rows2[i0:i1] = Xb.sum(1)
+        cost2 += float((C[i0:i1].to(torch.float64) * Xb).sum())
+    er = (p - rows2).clamp_min(0.0)
+    ec = (q - cols * ys).clamp_min(0.0)
+    s = float(er.sum())
+    if s > 0.0:
+        Cec = torch.zeros(m, dtype=torch.float64, device=dev)
+        for i0 in range(0, m, block_rows):
+            i1 = min(m, i0 + block_rows)
+            Cec[i0:i1] = C[i0:i1].to(torch.float64) @ ec
+        cost2 += float(er @ Cec) / s
+    lower = float(p @ mu + q @ cmin)
+    upper = cost2
+    return {"primal": primal, "upper_rounded_plan": upper, "lower_c_transform": lower,
+            "certified_rel_gap": (upper - lower) / abs(lower) if lower != 0 else None,
+            "moved_mass": s}
+
+
+def _device_problem(workload, seed, dev, m=None, n=None):
+    """The workload built on the GPU (bit-identical to the host builder) with an X buffer of the
+    same row pitch; returns (problem, C view, p, q, X view, mu, nu)."""
+    import torch
+
+    import workloads
+
+    spec = workloads.CONFIGS[workload]
+    nn = int(spec["n"] if n is None else n)
+    pr = workloads.make_problem(workload, seed=seed, m=m, n=n, device=dev, ld=workloads.pad_ld(nn))
+    C = pr.C[:, : pr.n]
+    ld = C.stride(0)
+    X = torch.empty((pr.m, ld), dtype=torch.float32, device=dev)[:, : pr.n]
+    p = torch.as_tensor(pr.p, device=dev)
+    q = torch.as_tensor(pr.q, device=dev)
+    mu = torch.zeros(pr.m, dtype=torch.float64, device=dev)
+    nu = torch.zeros(pr.n, dtype=torch.float64, device=dev)
+    return pr, C, p, q, X, mu, nu
+
+
+def _final(res):
+    return {k: res[k] for k in ("iters", "primal_obj", "dual_obj", "gap", "res_l1", "dual_res", "nnz")}
+
+
+def _full_rule_record(args, dev, local):
+    """One solve of `args.full_rule_workload` under the full stopping test (gap and l1 residual
+    <= tol), timed with CUDA events, with its certificate."""
+    import torch
+
+    from paper_2110_11738_b300 import drot
+
+    pr, C, p, q, X, mu, nu = _device_problem(args.full_rule_workload, args.seed, dev)
+    rule = drot.STOP_GAP | drot.STOP_RES_L1
+    with drot.Solver(device=local, stop_rule=rule, autotune=True) as s:
+        # the untimed first solve builds the plan and the graphs (a few iterations suffice)
+        s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=64, X=X, mu=mu, nu=nu, check=False)
+        s.reset_profile()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.full_rule_max_iter, X=X, mu=mu, nu=nu,
+                      check=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        secs = e0.elapsed_time(e1) / 1e3
+        prof = s.profile()
+    cert = _certificate(C, p, q, X, mu, nu)
+    # the same workload under the gap alone, for comparison
+    with drot.Solver(device=local, stop_rule=drot.STOP_GAP, autotune=True) as s:
+        s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=64, X=X, mu=mu, nu=nu, check=False)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        gres = s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu, check=False)
+        gsecs = time.perf_counter() - t0
+    gcert = _certificate(C, p, q, X, mu, nu)
+    out = {"workload": args.full_rule_workload, "m": pr.m, "n": pr.n, "rule": _rule_text("full"),
+           "tol": args.tol, "max_iter": args.full_rule_max_iter, "seconds": secs, "status": res["status_name"],
+           "ms_per_iter": secs * 1e3 / max(1, res["iters"]), "final": dict(_final(res), certificate=cert),
+           "clocks": clocks, "gpu_launches": int(prof["kernel_launches"]),
+           "gap_rule_same_workload": {"seconds": gsecs, "status": gres["status_name"],
+                                      "final": dict(_final(gres), certificate=gcert)}}
+    return out
 
 
 def run_ours(args):
@@ -243,17 +452,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    pr = workloads.make_problem(args.workload, seed=args.seed, device=dev, ld=workloads.pad_ld(
-        workloads.CONFIGS[args.workload]["n"]))
+    pr, C, p, q, X, mu, nu = _device_problem(args.workload, args.seed, dev)
     m, n = pr.m, pr.n
-    C = pr.C[:, :n]
     ld = C.stride(0)
-    p = torch.as_tensor(pr.p, device=dev)
-    q = torch.as_tensor(pr.q, device=dev)
-    Xbuf = torch.empty((m, ld), dtype=torch.float32, device=dev)
-    X = Xbuf[:, :n]
-    mu = torch.zeros(m, dtype=torch.float64, device=dev)
-    nu = torch.zeros(n, dtype=torch.float64, device=dev)
 
     rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
     solver = drot.Solver(device=local, profile=False, stop_rule=rule, step_variant=args.step_variant,
@@ -294,6 +495,8 @@ def run_ours(args):
     ms_per_solve = _max_over_ranks(elapsed_ms / args.steps, world, dev)
     iters = [r["iters"] for r in results]
     statuses = sorted({r["status_name"] for r in results})
+    final = _final(results[-1])
+    final["certificate"] = _certificate(C, p, q, X, mu, nu)
 
     # Second timed region: the same solve with a CUDA event recorded around every
     # fused-step launch inside the iteration graphs (the events sit between kernels, so
@@ -315,6 +518,7 @@ def run_ours(args):
     alg_bytes = (10 if args.c_skip else BYTES_PER_ENTRY) * m * n
     achieved = alg_bytes / (step_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
+    iter_ms = ms_per_solve / statistics.mean(iters)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -339,16 +543,29 @@ def run_ours(args):
                "iters": [r["iters"] for r in e_res]}
         del Ch, Xh
 
+    # the full stopping test on the 8192 x 6144 workload, and one batched solve
+    full_rule = None
+    if args.full_rule_workload != "none":
+        full_rule = _full_rule_record(args, dev, local)
+    batched = None
+    if args.batched_record:
+        batched = _batched_record(args, dev, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cb = _cpu_baseline(args.workload, args.seed, int(statistics.mean(iters)), args.sample_iters)
-            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            cpu = _cpu_baseline(args.workload, args.seed, int(round(statistics.mean(iters))), "GPU count, extrapolated",
+                                args.sample_iters, args.single_sample_iters, pr=pr)
         except MemoryError:
             cpu = None
 
     kernel_name = _step_kernel_name(pprof, args.c_skip)
     traffic = _traffic_per_launch(args.workload, kernel_name)
+    tol_met = {"gap": results[-1]["gap"] <= args.tol, "res_l1": results[-1]["res_l1"] <= args.tol,
+               "res_l1_at_stop": results[-1]["res_l1"],
+               "note": None if results[-1]["res_l1"] <= args.tol else
+               "the gap fell below tol while the plan's l1 marginal residual is still above it: see full_rule for "
+               "the time to both, and final.certificate for how far the stopped plan is from optimal"}
     line = {
         "metric": METRIC,
         "value": ms_per_solve / 1e3,
@@ -363,7 +580,7 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "n": n, "ld": ld, "seed": args.seed, "tol": args.tol,
-                   "rho": pr.rho, "stop_rule": {"gap": "gap<=tol", "full": "gap<=tol and l1 residual<=tol"}[args.stop],
+                   "rho": pr.rho, "stop_rule": _rule_text(args.stop),
                    "l2": f"inputs larger than L2 (C+X = {2 * m * ld * 4 / 1e6:.0f} MB > 126 MB)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "sums": "fixed-order partials" if args.deterministic else "FP64 atomics",
@@ -373,7 +590,8 @@ def run_ours(args):
                    "pass_order": "forward" if args.serpentine < 0 else "serpentine"},
         "iters_to_tol": iters,
         "status": statuses,
-        "ms_per_iter": ms_per_solve / statistics.mean(iters),
+        "tolerance_met": tol_met,
+        "ms_per_iter": iter_ms,
         "gpu_launches": int(prof["kernel_launches"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
@@ -381,7 +599,10 @@ def run_ours(args):
                      "step_ms": step_ms, "timed_launches": int(pprof["step_launches"]),
                      "finish_ms": pprof["finish_ms_total"] / max(1, pprof["step_launches"]),
                      "step_plus_finish_ms": pprof["iter_ms_total"] / max(1, pprof["step_launches"]),
-                     "timed_region": "separate profiled solve (events around each fused step)",
+                     "iter_ms": iter_ms,
+                     "iter_frac": alg_bytes / (iter_ms * 1e-3) / 1e9 / peak,
+                     "timed_region": "separate profiled solve (events around each fused step); iter_ms from the "
+                                     "main timed region (whole solves / iterations)",
                      "profiled_solve_ms": prof_wall_ms,
                      "alg_bytes_per_launch": alg_bytes,
                      "plan": {k: prof[k] for k in ("tile_k", "grid_ctas", "col_tiles", "graph_iters",
@@ -389,7 +610,9 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "final": {k: results[-1][k] for k in ("primal_obj", "dual_obj", "gap", "res_l1", "dual_res", "nnz")},
+        "final": final,
+        "full_rule": full_rule,
+        "batched": batched,
     }
     solver.close()
     if rank == 0:
@@ -405,7 +628,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="plain_8192x6144",
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["plain_8192x6144", "plain_256", "plain_20000", "batched_512", "warm_1024"])
     ap.add_argument("--batch", type=int, default=512, help="problems of the batched workload")
     ap.add_argument("--train-problems", type=int, default=32, help="warm_1024: problems the network is trained on")
@@ -424,10 +647,24 @@ def main(argv=None):
                     help="pass order of the register-fed step: 1 alternate, -1 forward only, 0 library default")
     ap.add_argument("--max-iter", type=int, default=3_000_000)
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--sample-iters", type=int, default=8)
+    ap.add_argument("--sample-iters", type=int, default=4,
+                    help="cpu_baseline: oracle iterations timed on all host cores")
+    ap.add_argument("--single-sample-iters", type=int, default=2,
+                    help="cpu_baseline: oracle iterations timed on one core")
+    ap.add_argument("--full-rule-workload", default="auto",
+                    choices=["auto", "none", "plain_8192x6144", "plain_256", "plain_20000"],
+                    help="workload of the full_rule sub-record (one solve to gap and l1 residual <= tol); "
+                         "auto: plain_8192x6144 on the default workload, none otherwise")
+    ap.add_argument("--full-rule-max-iter", type=int, default=3_000_000)
+    ap.add_argument("--batched-record", default="auto", choices=["auto", "on", "off"],
+                    help="one-solve batched sub-record; auto: on for the default workload only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
+    default_line = args.workload == DEFAULT_WORKLOAD
+    if args.full_rule_workload == "auto":
+        args.full_rule_workload = FULL_RULE_WORKLOAD if default_line else "none"
+    args.batched_record = args.batched_record == "on" or (args.batched_record == "auto" and default_line)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up solves", file=sys.stderr)
     if args.impl == "reference":
@@ -527,6 +764,72 @@ def run_warm(args):
     return 0
 
 
+def _batched_problems(specs, dev):
+    """Device buffers of a batch built by workloads.make_batch(device=...)."""
+    import torch
+
+    out = []
+    for pr in specs:
+        Cb = pr.C
+        out.append(dict(C=Cb[:, : pr.n], X=torch.zeros_like(Cb)[:, : pr.n], p=torch.as_tensor(pr.p, device=dev),
+                        q=torch.as_tensor(pr.q, device=dev), mu=torch.zeros(pr.m, dtype=torch.float64, device=dev),
+                        nu=torch.zeros(pr.n, dtype=torch.float64, device=dev), rho=pr.rho))
+    return out
+
+
+def _batched_summary(specs, res, ms, tol):
+    import numpy as np
+
+    iters = np.array([r["iters"] for r in res])
+    l1 = np.array([r["res_l1"] for r in res])
+    alg_bytes = float(sum(12.0 * pr.m * pr.n * r["iters"] for pr, r in zip(specs, res)))
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    return {
+        "iters_to_tol": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
+        "status": sorted({r["status_name"] for r in res}),
+        "res_l1_at_stop": {"median": float(np.median(l1)), "max": float(l1.max()),
+                           "share_le_tol": float((l1 <= tol).mean())},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "drot_batched_step_kernel (whole solve)",
+                     "alg_bytes": alg_bytes, "note": "12 B per entry per iteration of every unconverged problem, "
+                                                     "over the whole solve's CUDA-event time"},
+    }
+
+
+def _batched_record(args, dev, local):
+    """One solve of the 512-problem batch (gap rule), timed with CUDA events, as a sub-record."""
+    import torch
+
+    import workloads
+    from paper_2110_11738_b300 import drot
+
+    specs = workloads.make_batch(B=args.batch, seed=args.seed, device=dev)
+    probs = _batched_problems(specs, dev)
+    rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
+    with drot.Solver(device=local, stop_rule=rule, autotune=True) as s:
+        s.solve_batched(probs, tol=args.tol, max_iter=64, check=False)  # tile policy, graphs
+        s.reset_profile()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = s.solve_batched(probs, tol=args.tol, max_iter=args.max_iter, check=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        prof = s.profile()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": "batched_512", "B": len(specs), "seconds": ms / 1e3, "stop_rule": _rule_text(args.stop),
+           "total_entries": int(sum(pr.m * pr.n for pr in specs)), "gpu_launches": int(prof["kernel_launches"]),
+           "clocks": clocks}
+    out.update(_batched_summary(specs, res, ms, args.tol))
+    del probs, specs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_batched(args):
     """The batched workload: B independent problems (m, n uniform in [64, 2048]) solved together by
     drot_solve_batched; one step = the whole batch to the stopping test.  Also times the first 32
@@ -540,20 +843,8 @@ def run_batched(args):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    specs = workloads.make_batch(B=args.batch, seed=args.seed)
-
-    def device_batch():
-        out = []
-        for pr in specs:
-            ld = workloads.pad_ld(pr.n)
-            Cb = torch.zeros((pr.m, ld), dtype=torch.float32, device=dev)
-            Cb[:, : pr.n] = torch.as_tensor(pr.C, device=dev)
-            out.append(dict(C=Cb[:, : pr.n], X=torch.zeros_like(Cb)[:, : pr.n], p=torch.as_tensor(pr.p, device=dev),
-                            q=torch.as_tensor(pr.q, device=dev), mu=torch.zeros(pr.m, dtype=torch.float64, device=dev),
-                            nu=torch.zeros(pr.n, dtype=torch.float64, device=dev), rho=pr.rho))
-        return out
-
-    probs = device_batch()
+    specs = workloads.make_batch(B=args.batch, seed=args.seed, device=dev)
+    probs = _batched_problems(specs, dev)
     rule = {"gap": drot.STOP_GAP, "full": drot.STOP_GAP | drot.STOP_RES_L1}[args.stop]
     solver = drot.Solver(device=local, stop_rule=rule, autotune=not args.no_autotune, serpentine=args.serpentine)
     for _ in range(args.warmup):
@@ -573,10 +864,7 @@ def run_batched(args):
     prof = solver.profile()
     ms = ev0.elapsed_time(ev1) / args.steps
     res = results[-1]
-    iters = np.array([r["iters"] for r in res])
-    alg_bytes = float(sum(12.0 * pr.m * pr.n * r["iters"] for pr, r in zip(specs, res)))
-    achieved = alg_bytes / (ms * 1e-3) / 1e9
-    peak, peak_kind = _peaks()
+    summ = _batched_summary(specs, res, ms, args.tol)
     # plain (one problem at a time) on the first 32 problems, same stopping test
     sub = min(32, len(probs))
     torch.cuda.synchronize(dev)
@@ -597,12 +885,11 @@ def run_batched(args):
                    "tiles": "autotuned" if not args.no_autotune else "default",
                    "tol": args.tol, "stop_rule": args.stop, "total_entries": int(sum(pr.m * pr.n for pr in specs)),
                    "pass_order": "forward" if args.serpentine < 0 else "serpentine"},
-        "iters_to_tol": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
-        "status": sorted({r["status_name"] for r in res}),
+        "iters_to_tol": summ["iters_to_tol"],
+        "status": summ["status"],
+        "res_l1_at_stop": summ["res_l1_at_stop"],
         "gpu_launches": int(prof["kernel_launches"]),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "drot_batched_step_kernel (whole solve)",
-                     "alg_bytes": alg_bytes, "note": "12 B per entry per iteration of every unconverged problem"},
+        "roofline": summ["roofline"],
         "plain_vs_batched_first32_ms": {"plain": seq_ms, "batched": bat_ms},
         "clocks": clocks,
     }

@@ -87,3 +87,42 @@ def test_clock_samples_and_throttle_reasons():
     assert s.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     s.proc = None
     assert s.stop() is None
+
+
+def test_certificate_brackets_the_exact_optimum():
+    """The benchmark's optimality certificate: the rounded plan's cost is an upper bound and the
+    c-transform dual objective a lower bound of the exact LP optimum (HiGHS), for an optimal pair,
+    for an infeasible plan and for perturbed duals; both meet the optimum at an exact solution."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import workloads
+
+    pr = workloads.make_problem("plain_8192x6144", seed=3, m=9, n=7)
+    C64 = pr.C.astype(np.float64)
+    X, mu, nu, opt = oracle.lp_primal_dual(C64, pr.p, pr.q)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a))  # noqa: E731
+    C = t(pr.C)
+    cert = bench._certificate(C, t(pr.p), t(pr.q), t(X.astype(np.float32)), t(mu), t(nu), block_rows=4)
+    assert cert["lower_c_transform"] <= opt + 1e-9
+    assert cert["upper_rounded_plan"] >= opt - 1e-7
+    assert abs(cert["lower_c_transform"] - opt) <= 1e-9
+    assert abs(cert["upper_rounded_plan"] - opt) <= 1e-6
+    rng = np.random.default_rng(0)
+    for trial in range(5):
+        Xb = (X * rng.uniform(0.5, 1.5, size=X.shape) + rng.uniform(0, 1e-3, size=X.shape)).astype(np.float32)
+        mub = mu + rng.normal(0, 0.05, size=mu.shape)
+        c = bench._certificate(C, t(pr.p), t(pr.q), t(Xb), t(mub), t(nu), block_rows=3)
+        assert c["lower_c_transform"] <= opt + 1e-12
+        assert c["upper_rounded_plan"] >= opt - 1e-7
+        assert c["certified_rel_gap"] >= 0.0
+        # the rounded plan is feasible: recompute its cost independently
+        xs = np.minimum(pr.p / Xb.astype(np.float64).sum(1), 1.0)
+        X1 = Xb.astype(np.float64) * xs[:, None]
+        ys = np.minimum(pr.q / X1.sum(0), 1.0)
+        X2 = X1 * ys[None, :]
+        er, ec = pr.p - X2.sum(1), pr.q - X2.sum(0)
+        Xf = X2 + np.outer(er, ec) / er.sum()
+        assert np.abs(Xf.sum(1) - pr.p).max() < 1e-12 and np.abs(Xf.sum(0) - pr.q).max() < 1e-12
+        assert abs((C64 * Xf).sum() - c["upper_rounded_plan"]) < 1e-12

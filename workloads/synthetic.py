@@ -214,8 +214,11 @@ def make_problem(name: str, seed: int = 0, m: Optional[int] = None, n: Optional[
 
 
 def make_batch(name: str = "batched_512", seed: int = 0, B: Optional[int] = None,
-               mn_low: Optional[int] = None, mn_high: Optional[int] = None) -> list:
-    """Independent problems of uneven shape, m and n each uniform in [mn_low, mn_high]."""
+               mn_low: Optional[int] = None, mn_high: Optional[int] = None, device=None) -> list:
+    """Independent problems of uneven shape, m and n each uniform in [mn_low, mn_high].
+
+    ``device`` selects the torch cost builder (each C a float32 tensor of shape (m, pad_ld(n))
+    on that device, bit-identical to the NumPy one); without it C is a NumPy (m, n) array."""
     spec = dict(CONFIGS[name])
     B = int(spec["B"] if B is None else B)
     lo = int(spec["mn_low"] if mn_low is None else mn_low)
@@ -231,7 +234,10 @@ def make_batch(name: str = "batched_512", seed: int = 0, B: Optional[int] = None
         p = _marginal(r, m, spec["marginals"])
         q = _marginal(r, n, spec["marginals"])
         p, q = _rescale_mass(p, q)
-        C, scale = sq_euclidean_cost_np(x, y, return_scale=True)
+        if device is None:
+            C, scale = sq_euclidean_cost_np(x, y, return_scale=True)
+        else:
+            C, scale = sq_euclidean_cost_torch(x, y, device=device, ld=pad_ld(n), return_scale=True)
         probs.append(Problem(name=f"{name}[{b}]", seed=int(seeds[b]), m=m, n=n, C=C, p=p, q=q,
                              rho=default_rho(m, n, spec["rho0"]), tol=float(spec["tol"]), x=x, y=y,
                              cost_scale=float(scale)))
