@@ -45,8 +45,17 @@
  * and the result struct complete.
  *
  * Errors: every entry point returns a drot_status.  Invalid arguments are rejected on
- * the host before any launch.  No kernel in this library waits on another block or
- * another kernel, so an error cannot leave the device hung.
+ * the host before any launch.  Device-side waits exist and each one ends:
+ *   - software waits on other blocks poll a bounded number of times: the persistent
+ *     solve's grid barriers (drot_config.wait_limit, default 2^24 polls) and the TMA-fed
+ *     step's mbarrier ring (2^20 polls per wait).  A wait that runs out sets a fault flag
+ *     that makes every other block leave, and the call returns DROT_ERR_TIMEOUT with the
+ *     CUDA context still usable;
+ *   - the cluster-resident solve's hardware cluster barriers wait only on the CTAs of the
+ *     same cluster, which the hardware schedules together, and on nothing outside it;
+ *   - kernels chained by programmatic dependent launch wait (griddepcontrol.wait) for the
+ *     kernel before them on the same stream, which never waits on a later one.
+ * Kernels never trap; a NaN/Inf in the iteration ends the solve with DROT_ERR_NONFINITE.
  */
 #ifndef DROT_H
 #define DROT_H
@@ -83,7 +92,9 @@ typedef struct {
     int stop_rule;              /* bitmask of DROT_STOP_*; 0 selects DROT_STOP_GAP | DROT_STOP_RES_L1 */
     double rho0;                /* rho = rho0 / (m + n) when a call passes rho <= 0 (default 2, Sec. 4) */
     int graph_iters;            /* iterations per CUDA-graph replay; 0: chosen from the problem size */
-    int tile_k;                 /* float4 chunks per lane per row segment (1, 2 or 4); 0: automatic */
+    int tile_k;                 /* float4 chunks per lane per row segment (1, 2 or 4); 0: automatic.
+                                   drot_solve_batched: every problem of the batch takes this tile
+                                   width and the tile-policy autotuner is skipped */
     int grid_ctas;              /* CTAs of the fused step kernel; 0: automatic */
     int profile;                /* 1: time every fused-step launch with CUDA events (drot_get_profile) */
     int step_variant;           /* fused step: 1 register-fed (128-bit loads), 2 TMA-fed (bulk copies into a
@@ -228,11 +239,20 @@ drot_status drot_solve_batched(drot_handle *h, int32_t B, const drot_problem *pr
  *   - Size limit: the workspace is about 8*(3m + 2n + T*m) + 4096*(T + 2*SMs) + 8 KiB bytes with
  *     T = ceil(n/512) (n >= 1536; narrower problems use narrower tiles).  m = n = 20000 fits (~8 MB).
  *     A problem that does not fit returns DROT_ERR_TOO_LARGE before anything is launched.
+ *   - The array is placed in device memory when the CUDA runtime loads this library's device code on
+ *     that device, which under lazy module loading (the default) is the first use of the library
+ *     there - the first kernel launch or address lookup of any entry point.  A host that reserves all
+ *     free device memory up front must therefore make one call into this library on each device
+ *     before doing so (or run with CUDA_MODULE_LOADING=EAGER, which places it when the library is
+ *     loaded); otherwise that first call can fail with DROT_ERR_CUDA (out of memory).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
  *     device current).  Make that first call before any stream capture is started on the device.
- *   - Every call uses the same array.  Calls whose GPU work overlaps (other streams, other host
- *     threads) race on it and corrupt each other's results: serialise them.  Each call initialises
- *     every part of the array it reads, so nothing from an earlier call leaks into a later one.
+ *   - Every call on a device uses the same array.  Two calls whose GPU work overlapped would race on
+ *     it and corrupt each other's results, so the library prevents it: calls on the same device are
+ *     serialised by a lock inside the library (a second host thread blocks until the first call has
+ *     returned) and every call, error returns included, waits for its own GPU work before returning.
+ *     Calls on different devices do not block each other.  Each call initialises every part of the
+ *     array it reads, so nothing from an earlier call leaks into a later one.
  *   - Work is issued on `stream` (a cudaStream_t; NULL: the default stream) and the call returns
  *     after synchronising it, with X, mu, nu and *res (may be NULL) complete. */
 #define DROT_STATIC_SCRATCH_BYTES (16u << 20)

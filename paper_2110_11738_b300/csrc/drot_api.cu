@@ -1131,8 +1131,14 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     const int rule = (h->cfg.stop_rule & 7) ? (h->cfg.stop_rule & 7) : (DROT_STOP_GAP | DROT_STOP_RES_L1);
     int thr[2] = {kBatchPolicies[0][0], kBatchPolicies[0][1]};
     const unsigned long long sig = batch_signature(pr, B);
-    const bool tuned = h->cfg.autotune && h->batch_tuned_sig == sig;
-    if (tuned) {
+    // an explicit tile_k gives every problem that tile width (no tuning)
+    const bool forced_k = h->cfg.tile_k == 1 || h->cfg.tile_k == 2 || h->cfg.tile_k == 4;
+    const bool tuned = forced_k || (h->cfg.autotune && h->batch_tuned_sig == sig);
+    if (forced_k) {
+        const long long big = 1LL << 30;
+        thr[0] = h->cfg.tile_k == 1 ? (int)big : 0;
+        thr[1] = h->cfg.tile_k <= 2 ? (int)big : 0;
+    } else if (tuned) {
         thr[0] = h->batch_k_thresholds[0];
         thr[1] = h->batch_k_thresholds[1];
     }
@@ -1742,23 +1748,29 @@ constexpr int kStaticMaxDevices = 64;
 constexpr int kStaticMaxCtas = 512;
 constexpr int kStaticMaxTiles = 8192;
 
-std::mutex g_static_mu;       // guards the per-device address table
-std::mutex g_static_call_mu;  // serialises calls (they share the workspace and the host tables)
-void *g_static_addr[kStaticMaxDevices] = {};
-long long g_static_wbound[kStaticMaxCtas + 1];
-int g_static_slot_base[kStaticMaxCtas];
-int g_static_tile_slot[kStaticMaxTiles + 1];
+// Host state of one device: the lock that serialises the calls on that device (they share
+// its workspace and these launch tables) and the workspace's device address.
+struct StaticDeviceState {
+    std::mutex call_mu;
+    void *addr = nullptr;
+    long long wbound[kStaticMaxCtas + 1];
+    int slot_base[kStaticMaxCtas];
+    int tile_slot[kStaticMaxTiles + 1];
+};
+std::mutex g_static_mu;  // guards the address lookups
+StaticDeviceState g_static_dev[kStaticMaxDevices];
 
-// Device address of the static workspace on `dev` (looked up once per device).
+// Device address of the static workspace on `dev` (looked up once per device, with `dev`
+// current: the caller's current device).
 cudaError_t static_workspace(int dev, void **out) {
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    if (!g_static_dev[dev].addr) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, drot_static_scratch);
         if (e != cudaSuccess) return e;
-        g_static_addr[dev] = ptr;
+        g_static_dev[dev].addr = ptr;
     }
-    *out = g_static_addr[dev];
+    *out = g_static_dev[dev].addr;
     return cudaSuccess;
 }
 
@@ -1795,10 +1807,11 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
     const int G = (int)std::min<long long>(
         std::min<long long>(2LL * num_sms, kStaticMaxCtas),
         std::max<long long>(1, (units + drot::kWarps - 1) / drot::kWarps));
-    std::lock_guard<std::mutex> call_lock(g_static_call_mu);
-    long long *wbound = g_static_wbound;
-    int *slot_base = g_static_slot_base;
-    int *tile_slot = g_static_tile_slot;
+    StaticDeviceState &ds = g_static_dev[dev];
+    std::lock_guard<std::mutex> call_lock(ds.call_mu);
+    long long *wbound = ds.wbound;
+    int *slot_base = ds.slot_base;
+    int *tile_slot = ds.tile_slot;
     const SegCost cost(m, T, TW, n);
     const double total_cost = cost.total();
     wbound[0] = 0;
@@ -1842,9 +1855,14 @@ extern "C" drot_status drot_solve_static(int64_t m, int64_t n, const float *C, i
     int *d_slot_base = carve<int>(cur, G);
     int *d_tile_slot = carve<int>(cur, T + 1);
 
-#define STATIC_CUDA(call)                                  \
-    do {                                                   \
-        if ((call) != cudaSuccess) return DROT_ERR_CUDA;   \
+    // On a failed call, wait for the work already queued on the stream before returning:
+    // the next call (on any thread, once the lock is released) reuses the workspace.
+#define STATIC_CUDA(call)                              \
+    do {                                               \
+        if ((call) != cudaSuccess) {                   \
+            cudaStreamSynchronize(stream);             \
+            return DROT_ERR_CUDA;                      \
+        }                                              \
     } while (0)
 
     STATIC_CUDA(cudaMemcpyAsync(d_wbound, wbound, sizeof(long long) * (G + 1), cudaMemcpyHostToDevice, stream));

@@ -6,10 +6,11 @@ framework's memory pool, or a latency-critical loop that must never enter the al
 callers pass only their inputs and outputs; the workspace is a fixed 16 MiB array inside the
 library.
 
-The test calls the entry point twice in a row through the C ABI (a cold solve to tolerance, then
+The first test calls the entry point twice in a row through the C ABI (a cold solve to tolerance, then
 a few warm-started iterations on another, ragged shape) and compares each result with drot_solve
 on the same inputs, within the tolerances the other parity tests use.  It also checks that a
-problem whose workspace does not fit is refused before anything runs.  This file is collected
+problem whose workspace does not fit is refused before anything runs, and that a call after the
+first leaves the device's free memory unchanged.  This file is collected
 last so that a failing run stopped at the first failure has already run every other test.
 """
 
@@ -86,3 +87,26 @@ def test_static_solve_refuses_a_problem_larger_than_its_workspace():
     got = drot.drot_solve_static(C, p, q, tol=1e-6, max_iter=10, X=X, mu=mu, nu=nu)
     assert got["status"] == drot.DROT_ERR_TOO_LARGE
     assert float(X.min()) == 3.0  # nothing ran
+
+
+def test_static_solve_allocates_no_device_memory():
+    """The property the entry point exists for: after a first call (which places the library's
+    device code and its fixed array), further calls leave the device's free memory and torch's
+    allocator untouched."""
+    torch.cuda.set_device(0)
+    pr = workloads.make_problem("plain_8192x6144", seed=11, m=300, n=517)
+    C, p, q, X, mu, nu = _inputs(pr)
+    first = drot.drot_solve_static(C, p, q, rho=pr.rho, tol=1e-6, max_iter=2000, X=X, mu=mu, nu=nu)
+    assert first["status"] in (drot.DROT_OK, drot.DROT_NOT_CONVERGED), first
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    allocated_before = torch.cuda.memory_allocated()
+    reserved_before = torch.cuda.memory_reserved()
+    second = drot.drot_solve_static(C, p, q, rho=pr.rho, tol=1e-6, max_iter=2000, X=X, mu=mu, nu=nu)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert second["status"] == first["status"]
+    assert abs(second["primal_obj"] - first["primal_obj"]) <= 1e-5 * abs(first["primal_obj"])
+    assert free_after == free_before
+    assert torch.cuda.memory_allocated() == allocated_before
+    assert torch.cuda.memory_reserved() == reserved_before
