@@ -141,7 +141,7 @@ def warm_solve(net: drot.Mlp, solver: drot.Solver, pr, tol: float, max_iter: int
     net.warm_start(xs, yt, d["p"], d["q"], pr.cost_scale, d["C"], d["X"], d["mu"], d["nu"])
     out = solver.solve(d["C"], d["p"], d["q"], rho=pr.rho, tol=tol, max_iter=max_iter, X=d["X"], mu=d["mu"],
                        nu=d["nu"], warm=True, check=False)
-    out["seeded"] = True
+    out.update(C=d["C"], p=d["p"], q=d["q"], seeded=True)
     if fallback and out["status"] != drot.DROT_OK:
         out = cold_solve(solver, pr, tol, max_iter, device)
         out["seeded"] = False
@@ -149,6 +149,10 @@ def warm_solve(net: drot.Mlp, solver: drot.Solver, pr, tol: float, max_iter: int
 
 
 def cold_solve(solver: drot.Solver, pr, tol: float, max_iter: int, device=0):
+    """The paper's plain solve from X_0 = p q^T; the result dict also carries the problem's device
+    buffers C, p, q."""
     d = _device_problem(pr, device)
-    return solver.solve(d["C"], d["p"], d["q"], rho=pr.rho, tol=tol, max_iter=max_iter, X=d["X"], mu=d["mu"],
-                        nu=d["nu"], check=False)
+    out = solver.solve(d["C"], d["p"], d["q"], rho=pr.rho, tol=tol, max_iter=max_iter, X=d["X"], mu=d["mu"],
+                       nu=d["nu"], check=False)
+    out.update(C=d["C"], p=d["p"], q=d["q"])
+    return out

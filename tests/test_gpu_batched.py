@@ -37,8 +37,10 @@ def _shapes():
 
 # default: alternating pass directions within each graph; graph_iters=1: one iteration per
 # replay, so the direction comes from the parity word the host rewrites between replays;
-# serpentine=-1: every pass forwards
-@pytest.mark.parametrize("cfg", [{}, {"graph_iters": 1}, {"serpentine": -1}])
+# serpentine=-1: every pass forwards; tile_k 1 and 2: 128- and 256-column tiles for every
+# problem (the step kernel's narrower tile widths, which the tile-policy autotuner may pick)
+@pytest.mark.parametrize("cfg", [{}, {"graph_iters": 1}, {"serpentine": -1}, {"tile_k": 1}, {"tile_k": 2},
+                                 {"tile_k": 1, "serpentine": -1}])
 def test_batched_step_parity_with_oracle(cfg):
     probs, starts, specs = [], [], []
     for b, (m, n) in enumerate(_shapes()):

