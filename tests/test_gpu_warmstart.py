@@ -206,13 +206,15 @@ def test_trained_network_predicts_duals_and_full_rule_solves_take_as_long_as_col
     assert 2.0 / 3.0 <= ratio <= 1.5, (cold, warm)
 
 
-def test_gap_rule_seeded_solves_stop_sooner_at_plans_no_less_feasible(trained_mixture_net):
+def test_gap_rule_seeded_solves_stop_sooner_but_neither_stop_is_a_solution(trained_mixture_net):
     """Under the duality gap alone (the metric's condition) the seeded solves stop after fewer
-    iterations than cold ones on average, and their plans at the stop are no less feasible (mean
-    l1 residual within 1.5x of the cold solves').  Neither side's stop is a solution: the gap
-    falls below 1e-6 where primal and dual objectives cross, with l1 residuals of order 1e-3 on
-    this family (measured on B300: mean iterations 2073 cold vs 1355 warm, mean l1 6.4e-3 vs
-    6.0e-3), which is why the library's default test also requires the l1 residual."""
+    iterations than cold ones on average, but the gap test fires where primal and dual objectives
+    cross, and on this family both kinds of stop leave the plan's marginals far from met: the
+    mean l1 residual at the stop exceeds 100 x tol on both sides.  How feasible a stop is varies
+    from problem to problem and from run to run (measured on B300 over the same eight problems:
+    mean l1 6.4e-3 cold against 6.0e-3 and 1.6e-2 warm in two runs whose networks differed only
+    through the order of atomic additions in the labels, features and gradients), so no ordering
+    of the two residuals is asserted; the library's default test requires the l1 residual too."""
     net, _ = trained_mixture_net
     cold, warm = [], []
     with drot.Solver(device=0, stop_rule=drot.STOP_GAP) as solver:
@@ -224,4 +226,4 @@ def test_gap_rule_seeded_solves_stop_sooner_at_plans_no_less_feasible(trained_mi
             warm.append((w["iters"], w["res_l1"]))
     print(f"warm-start, gap rule at 1e-6: (iterations, l1 at stop) cold {cold} warm {warm}")
     assert np.mean([w[0] for w in warm]) < np.mean([c[0] for c in cold])
-    assert np.mean([w[1] for w in warm]) <= 1.5 * np.mean([c[1] for c in cold])
+    assert np.mean([c[1] for c in cold]) > 100 * 1e-6 and np.mean([w[1] for w in warm]) > 100 * 1e-6
