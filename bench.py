@@ -17,7 +17,9 @@ objectives cross), so the line also carries:
   full_rule       one solve under the full test (gap and l1 residual <= tol) of the
                   8192 x 6144 workload, with its time, iterations, status and certificate;
   batched         one solve of the 512-problem batch (one problem per uneven shape)
-                  with the fraction of the HBM roofline over the whole solve.
+                  with the fraction of the HBM roofline over the whole solve;
+  c_skip          one solve of the default workload with C-load skipping (Claim 1 of
+                  Sec. 3.3: 10 instead of 12 bytes per entry on average).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -448,6 +450,41 @@ def _full_rule_record(args, dev, local):
     return out
 
 
+def _c_skip_record(args, C, p, q, X, mu, nu, pr, local, rule):
+    """One solve of the default workload with C-load skipping (Claim 1, Sec. 3.3): passes alternate
+    between reading X and C (storing X - rho C) and reading that array alone, 10 bytes per entry
+    on average; the stopping test runs after the C-reading passes.  Timed with CUDA events, and
+    once more with events around every fused-step launch for its roofline (10 B per entry)."""
+    import torch
+
+    from paper_2110_11738_b300 import drot
+
+    dev = torch.device("cuda", local)
+    with drot.Solver(device=local, stop_rule=rule, c_skip=True) as s:
+        s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)  # warm-up
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        secs = e0.elapsed_time(e1) / 1e3
+        plan = s.profile()
+    with drot.Solver(device=local, stop_rule=rule, c_skip=True, profile=True, tile_k=plan["tile_k"]) as s:
+        s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
+        s.reset_profile()
+        s.solve(C, p, q, rho=pr.rho, tol=args.tol, max_iter=args.max_iter, X=X, mu=mu, nu=nu)
+        prof = s.profile()
+    step_ms = prof["step_ms_total"] / max(1, prof["step_launches"])
+    achieved = 10.0 * pr.m * pr.n / (step_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    return {"seconds": secs, "iters": res["iters"], "status": res["status_name"],
+            "ms_per_iter": secs * 1e3 / max(1, res["iters"]), "final": _final(res),
+            "roofline": {"bound": "hbm", "alg_bytes_per_entry": 10, "step_ms": step_ms, "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "drot_step_kernel<%d,1,1|2>" % prof["tile_k"]}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -554,6 +591,11 @@ def run_ours(args):
                "iters": [r["iters"] for r in e_res]}
         del Ch, Xh
 
+    # C-load skipping (Claim 1) on the same workload
+    c_skip_rec = None
+    if args.c_skip_record and not args.c_skip:
+        c_skip_rec = _c_skip_record(args, C, p, q, X, mu, nu, pr, local, rule)
+
     # the full stopping test on the 8192 x 6144 workload, and one batched solve
     full_rule = None
     if args.full_rule_workload != "none":
@@ -622,6 +664,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "final": final,
+        "c_skip": c_skip_rec,
         "full_rule": full_rule,
         "batched": batched,
     }
@@ -672,6 +715,8 @@ def main(argv=None):
     ap.add_argument("--full-rule-max-iter", type=int, default=3_000_000)
     ap.add_argument("--batched-record", default="auto", choices=["auto", "on", "off"],
                     help="one-solve batched sub-record; auto: on for the default workload only")
+    ap.add_argument("--c-skip-record", default="auto", choices=["auto", "on", "off"],
+                    help="one solve with C-load skipping on the same workload; auto: default workload only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
@@ -679,6 +724,7 @@ def main(argv=None):
     if args.full_rule_workload == "auto":
         args.full_rule_workload = FULL_RULE_WORKLOAD if default_line else "none"
     args.batched_record = args.batched_record == "on" or (args.batched_record == "auto" and default_line)
+    args.c_skip_record = args.c_skip_record == "on" or (args.c_skip_record == "auto" and default_line)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up solves", file=sys.stderr)
     if args.impl == "reference":

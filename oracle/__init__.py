@@ -109,14 +109,16 @@ def set_mutation(k: int) -> None:
 
 
 def drot_solve(C, p, q, rho, tol, max_iter, X0=None, mu0=None, nu0=None,
-               stop_on_dual_residual=False, history=False, stop_rule=None):
+               stop_on_dual_residual=False, history=False, stop_rule=None, all_cores=False):
     """Run Algorithm 1 from X0 = p q^T (or from a warm start) until the stop rule.
 
     ``stop_rule`` is a bitmask (1 gap, 2 l1 residual, 4 r_dual; default 3, or 7 with
-    ``stop_on_dual_residual``).  Returns a dict with X, mu, nu (FP64), iters, status, stats (dict) and,
+    ``stop_on_dual_residual``).  ``all_cores`` runs the OpenMP build of the same source (every
+    X_ij, r_i, s_j formed as in the single-thread build; only the three scalar totals are summed
+    in another order).  Returns a dict with X, mu, nu (FP64), iters, status, stats (dict) and,
     when ``history`` is true, the per-iteration stats as an (iters, 7) array.
     """
-    lib = _load()
+    lib = _load(all_cores)
     C = np.ascontiguousarray(np.asarray(C, dtype=np.float64))
     p = np.ascontiguousarray(np.asarray(p, dtype=np.float64))
     q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))

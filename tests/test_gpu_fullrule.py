@@ -3,7 +3,8 @@ and a long step-parity run at the full 8192 x 6144 size.
 
 Full-rule parity: the oracle's solves to gap <= 1e-6 AND l1 marginal residual <= 1e-6
 (Sec. 3.1, "Stopping criteria") are stored under tests/golden/fullrule_*.json by
-tests/golden/make_fullrule_golden.py (single-threaded FP64 oracle; hours at 1536 x 2048).
+tests/golden/make_fullrule_golden.py (FP64 oracle: single-threaded up to 768 x 1024, its OpenMP
+build at 1536 x 2048).
 The GPU solves the same problem (checked by the input hash) with the configuration the
 benchmark uses: automatic plan with the autotuner, all CTAs of the fused step, several
 512-column tiles, serpentine passes, FP64 atomic totals.  Bounds: objective within 1e-5
