@@ -59,7 +59,7 @@ def _gpu_buffers(pr):
 
 def test_every_golden_case_is_committed():
     names = {os.path.basename(g)[len("fullrule_"):-len(".json")] for g in GOLDEN}
-    assert {"gauss_384x512"} <= names, names
+    assert {"gauss_384x512", "gauss_768x1024"} <= names, names
 
 
 @pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(g)[9:-5] for g in GOLDEN])
