@@ -720,7 +720,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
-    default_line = args.workload == DEFAULT_WORKLOAD
+    # the sub-records (minutes of extra work) belong to the single-GPU default line only: under
+    # torchrun every rank would repeat them
+    default_line = args.workload == DEFAULT_WORKLOAD and _dist()[0] == 1
     if args.full_rule_workload == "auto":
         args.full_rule_workload = FULL_RULE_WORKLOAD if default_line else "none"
     args.batched_record = args.batched_record == "on" or (args.batched_record == "auto" and default_line)

@@ -1357,9 +1357,12 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     };
     auto pick_gi = [&](const std::vector<int> &act) {
         if (h->cfg.graph_iters > 0) return h->cfg.graph_iters;
+        // ~32 ms of the work still active per replay: the host reads every problem's flag
+        // between replays, and on the 512-problem workload shorter replays (4 ms: one
+        // iteration while all are active) cost 0.7 % of the solve in those round trips
         double bytes = 0.0;
         for (int b : act) bytes += 12.0 * (double)pr[b].m * (double)pr[b].n;
-        const double want = 4.0e-3 / (bytes / 6.0e12 + 12.0e-6);
+        const double want = 32.0e-3 / (bytes / 6.0e12 + 12.0e-6);
         int g = 1;
         while (g < 256 && 4.0 * g <= want) g *= 4;
         return g;

@@ -154,8 +154,10 @@ def test_step_parity_full_size_8192x6144(solver):
 
 @pytest.mark.slow
 def test_step_parity_full_size_20000(solver):
+    # three passes: forward, backward (serpentine order) and forward again over 40 column tiles
+    # (the last one 32 columns wide), every CTA of the fused step
     pr = workloads.make_problem("plain_20000", seed=0)
-    _step_parity(solver, pr, 1, seed=2)
+    _step_parity(solver, pr, 3, seed=2)
 
 
 def _solve_parity(solver, pr, tol=1e-6, rel_obj=1e-5):
