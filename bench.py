@@ -883,7 +883,7 @@ def _batched_summary(specs, res, ms, tol):
         "res_l1_at_stop": {"median": float(np.median(l1)), "max": float(l1.max()),
                            "share_le_tol": float((l1 <= tol).mean())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind, "kernel": "drot_batched_step_kernel (whole solve)",
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "drot_batched_step_kernel + drot_batched_narrow_kernel (whole solve)",
                      "alg_bytes": alg_bytes, "note": "12 B per entry per iteration of every unconverged problem, "
                                                      "over the whole solve's CUDA-event time"},
     }

@@ -141,6 +141,10 @@ typedef struct {
                                    pass forwards, 0 automatic (alternate).  Changes only the order in which
                                    partial sums are formed, hence the last bits of a run.  Also applies
                                    to drot_solve_batched; the FP64 solve always walks forwards */
+    int batch_narrow;           /* drot_solve_batched: tiles with at most 256 valid columns go to a second
+                                   kernel that packs two or four rows into one warp iteration.  0 automatic
+                                   (while the active problems' narrow tiles hold at least 65536 rows: below
+                                   that the extra launch costs more than packing saves), 1 always, -1 never */
 } drot_config;
 
 typedef struct {

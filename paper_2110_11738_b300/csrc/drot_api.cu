@@ -79,12 +79,19 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr double kRowTripCols = 1536.0;
 constexpr double kTileSwitchCols = 64.0 * (512.0 + kRowTripCols);
 
+// Rows the batched narrow-tile kernel packs into one warp iteration for a tile of w valid
+// columns (w <= 256): four up to 128 columns, two up to 256.
+inline int packed_rows(long long w) { return w <= 128 ? 4 : (w <= 256 ? 2 : 1); }
+
 struct SegCost {
     long long m, T, TW, last_w;
     double full, last, sw;  // cost of a row segment of a full tile / of the last tile; of a tile start
-    SegCost(long long m_, long long T_, long long TW_, long long n)
-        : m(m_), T(T_), TW(TW_), last_w(n - (T_ - 1) * TW_), full((double)TW_ + kRowTripCols),
-          last((double)last_w + kRowTripCols), sw(kTileSwitchCols) {}
+    // pack: segments of the narrow-tile kernel, whose round-trip charge is shared by the rows
+    // one warp iteration packs
+    SegCost(long long m_, long long T_, long long TW_, long long n, bool pack = false)
+        : m(m_), T(T_), TW(TW_), last_w(n - (T_ - 1) * TW_),
+          full((double)TW_ + kRowTripCols / (pack ? packed_rows(TW_) : 1)),
+          last((double)last_w + kRowTripCols / (pack ? packed_rows(last_w) : 1)), sw(kTileSwitchCols) {}
     // Cost of the first u segments (tile-major order).
     double before(long long u) const {
         const long long full_units = (T - 1) * m;
@@ -1033,7 +1040,19 @@ struct BatchLists {
     std::vector<long long> unit0;   // nactive + 1
     std::vector<long long> wbound;  // G + 1
     std::vector<int> fin_prob, fin_local;  // FB
+    // the narrow tiles' list (drot_batched_narrow_kernel); empty unless split
+    bool split = false;
+    std::vector<int> active_n;
+    std::vector<long long> unit0_n;   // nactive_n + 1
+    std::vector<long long> wbound_n;  // G + 1
 };
+
+// Wide tiles of a problem (more than 256 valid columns) come first; the others are narrow.
+int wide_tiles(long long n, int K, int T) {
+    if (K < 4) return 0;  // 128- and 256-column tiles are all narrow
+    const long long last_w = n - (long long)(T - 1) * 128LL * K;
+    return last_w <= 256 ? T - 1 : T;
+}
 
 // Tile width policy: K = 1 for n < t0, 2 for n < t1, else 4.
 int batch_k(long long n, const int thr[2]) { return n < thr[0] ? 1 : (n < thr[1] ? 2 : 4); }
@@ -1063,38 +1082,74 @@ unsigned long long batch_signature(const drot_problem *pr, int B) {
     return x ? x : 1ull;
 }
 
-// Segment list, cost-balanced CTA ranges (SegCost) and finish-block groups of the active problems.
-void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector<int> &active, int G, int FB,
-                       BatchLists &L) {
-    L.active = active;
-    const int na = (int)active.size();
-    L.unit0.assign(na + 1, 0);
-    std::vector<double> cost0(na + 1, 0.0);
-    for (int a = 0; a < na; ++a) {
-        const drot::BatchProb &P = hp[active[a]];
-        const long long units = (long long)P.T * P.m;
-        L.unit0[a + 1] = L.unit0[a] + units;
-        cost0[a + 1] = cost0[a] + SegCost(P.m, P.T, 128LL * P.K, P.n).total();
+// Segment lists (wide tiles, narrow tiles), cost-balanced CTA ranges (SegCost) and
+// finish-block groups of the active problems.
+namespace {
+// One list: the problems with segments in it, their first segments and the CTA ranges.
+// part(P) gives the (tiles, first column count of those tiles, width sum) the list holds.
+template <typename Part>
+void build_list(const std::vector<drot::BatchProb> &hp, const std::vector<int> &active, int G, bool pack,
+                Part part, std::vector<int> &act, std::vector<long long> &unit0, std::vector<long long> &wbound) {
+    act.clear();
+    unit0.assign(1, 0);
+    std::vector<double> cost0(1, 0.0);
+    std::vector<SegCost> costs;
+    for (int b : active) {
+        const drot::BatchProb &P = hp[b];
+        long long tiles = 0, cols = 0;
+        part(P, tiles, cols);
+        if (tiles <= 0) continue;
+        act.push_back(b);
+        unit0.push_back(unit0.back() + tiles * P.m);
+        costs.emplace_back(P.m, tiles, 128LL * P.K, cols, pack);
+        cost0.push_back(cost0.back() + costs.back().total());
     }
-    const long long total = L.unit0[na];
-    L.wbound.assign(G + 1, total);
-    L.wbound[0] = 0;
+    const int na = (int)act.size();
+    const long long total = unit0[na];
+    wbound.assign(G + 1, total);
+    wbound[0] = 0;
     int a = 0;
     for (int g = 1; g < G; ++g) {
         const double target = cost0[na] * g / G;
         while (a + 1 < na && cost0[a + 1] <= target) ++a;
         long long u = total;
-        if (na > 0) {
-            const drot::BatchProb &P = hp[active[a]];
-            u = L.unit0[a] + SegCost(P.m, P.T, 128LL * P.K, P.n).units_for(target - cost0[a]);
-        }
-        L.wbound[g] = std::max(L.wbound[g - 1], std::min(u, total));
+        if (na > 0) u = unit0[a] + costs[a].units_for(target - cost0[a]);
+        wbound[g] = std::max(wbound[g - 1], std::min(u, total));
     }
-    L.wbound[G] = total;
+    wbound[G] = total;
+}
+}  // namespace
+
+// The narrow-tile kernel is a launch of its own, a few µs per iteration whatever its work;
+// it pays only while the narrow tiles hold enough rows (packing saves ~0.2 ns per row on
+// B300).  Below this many rows the wide-tile kernel takes every tile, unpacked.
+constexpr long long kSplitRows = 65536;
+
+void build_batch_lists(const std::vector<drot::BatchProb> &hp, const std::vector<int> &active, int G, int FB,
+                       BatchLists &L, int narrow_mode) {
+    long long narrow_rows = 0;
+    for (int b : active) narrow_rows += (long long)(hp[b].T - hp[b].Tw) * hp[b].m;
+    L.split = narrow_rows > 0 && (narrow_mode > 0 || (narrow_mode == 0 && narrow_rows >= kSplitRows));
+    const bool split = L.split;
+    // wide tiles 0 .. Tw-1 (all of them full width but a ragged last one wider than 256);
+    // every tile when the narrow ones are not split off
+    build_list(hp, active, G, false,
+               [split](const drot::BatchProb &P, long long &tiles, long long &cols) {
+                   tiles = split ? P.Tw : P.T;
+                   cols = split ? std::min(P.n, (long long)P.Tw * 128LL * P.K) : P.n;
+               },
+               L.active, L.unit0, L.wbound);
+    // narrow tiles Tw .. T-1
+    build_list(hp, active, G, true,
+               [split](const drot::BatchProb &P, long long &tiles, long long &cols) {
+                   tiles = split ? P.T - P.Tw : 0;
+                   cols = P.n - (long long)P.Tw * 128LL * P.K;
+               },
+               L.active_n, L.unit0_n, L.wbound_n);
     L.fin_prob.assign(FB, -1);
     L.fin_local.assign(FB, 0);
     int fb = 0;
-    for (int x = 0; x < na; ++x) {
+    for (int x = 0; x < (int)active.size(); ++x) {
         const drot::BatchProb &P = hp[active[x]];
         for (int l = 0; l < P.fin_blocks && fb < FB; ++l, ++fb) {
             L.fin_prob[fb] = active[x];
@@ -1107,6 +1162,8 @@ struct BatchDev {
     drot::BatchProb *probs;
     int *active, *nactive, *parity, *fin_prob, *fin_local, *flags;
     long long *unit0, *wbound;
+    int *active_n, *nactive_n;
+    long long *unit0_n, *wbound_n;
 };
 
 drot_status upload_lists(drot_handle *h, const BatchLists &L, const BatchDev &D, int FB) {
@@ -1121,6 +1178,15 @@ drot_status upload_lists(drot_handle *h, const BatchLists &L, const BatchDev &D,
     DROT_CUDA(h, cudaMemcpyAsync(D.fin_prob, L.fin_prob.data(), sizeof(int) * FB, cudaMemcpyHostToDevice, h->stream));
     DROT_CUDA(h, cudaMemcpyAsync(D.fin_local, L.fin_local.data(), sizeof(int) * FB, cudaMemcpyHostToDevice,
                                  h->stream));
+    const int nn = (int)L.active_n.size();
+    DROT_CUDA(h, cudaMemcpyAsync(D.nactive_n, &nn, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (nn > 0)
+        DROT_CUDA(h, cudaMemcpyAsync(D.active_n, L.active_n.data(), sizeof(int) * nn, cudaMemcpyHostToDevice,
+                                     h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(D.unit0_n, L.unit0_n.data(), sizeof(long long) * (nn + 1), cudaMemcpyHostToDevice,
+                                 h->stream));
+    DROT_CUDA(h, cudaMemcpyAsync(D.wbound_n, L.wbound_n.data(), sizeof(long long) * L.wbound_n.size(),
+                                 cudaMemcpyHostToDevice, h->stream));
     // pageable sources: the copies return once the host data has been staged, but keep
     // the stream ordered with the next launch anyway
     return DROT_OK;
@@ -1162,9 +1228,9 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, drot::drot_batched_step_kernel<true>, drot::kThreads, 0);
     const int G = std::max(1, occ) * h->num_sms;
-    const size_t tables = align_up(sizeof(drot::BatchProb) * B, 256) + align_up(sizeof(int) * B, 256) * 3 +
-                          align_up(sizeof(long long) * (B + 1), 256) + align_up(sizeof(long long) * (G + 1), 256) +
-                          align_up(sizeof(int) * FB, 256) * 2 + 256;
+    const size_t tables = align_up(sizeof(drot::BatchProb) * B, 256) + align_up(sizeof(int) * B, 256) * 4 +
+                          align_up(sizeof(long long) * (B + 1), 256) * 2 + align_up(sizeof(long long) * (G + 1), 256) * 2 +
+                          align_up(sizeof(int) * FB, 256) * 2 + 256 * 2;
     drot_status st = arena_reserve(h, h->batch, bytes + tables);
     if (st != DROT_OK) return st;
     if (h->h_bstat_cap < (size_t)B) {
@@ -1202,6 +1268,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         P.inv_m = 1.0 / (double)m;
         P.K = batch_k(n, thr);
         P.T = (int)((n + 128LL * P.K - 1) / (128LL * P.K));
+        P.Tw = wide_tiles(n, P.K, P.T);
     }
     char *cur = base + bytes;
     BatchDev D{};
@@ -1214,6 +1281,10 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     D.wbound = carve<long long>(cur, G + 1);
     D.nactive = carve<int>(cur, 1);
     D.parity = carve<int>(cur, 1);
+    D.active_n = carve<int>(cur, B);
+    D.unit0_n = carve<long long>(cur, B + 1);
+    D.wbound_n = carve<long long>(cur, G + 1);
+    D.nactive_n = carve<int>(cur, 1);
 
     // scalar state of every problem, then the marginal checks
     std::vector<Scalars> hs(B);
@@ -1256,6 +1327,10 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
     A.fin_local = D.fin_local;
     A.nactive = D.nactive;
     A.parity = D.parity;
+    A.active_n = D.active_n;
+    A.unit0_n = D.unit0_n;
+    A.wbound_n = D.wbound_n;
+    A.nactive_n = D.nactive_n;
     A.warm = warm;
     A.serp = h->cfg.serpentine >= 0 ? 1 : 0;
     A.odd = 0;
@@ -1276,6 +1351,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
             for (int b = 0; b < B; ++b) {
                 hp[b].K = batch_k(hp[b].n, kBatchPolicies[pi]);
                 hp[b].T = (int)((hp[b].n + 128LL * hp[b].K - 1) / (128LL * hp[b].K));
+                hp[b].Tw = wide_tiles(hp[b].n, hp[b].K, hp[b].T);
             }
             cudaError_t e = cudaMemcpyAsync(D.probs, hp.data(), sizeof(drot::BatchProb) * B, cudaMemcpyHostToDevice,
                                             h->stream);
@@ -1284,17 +1360,19 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
                 break;
             }
             BatchLists TL;
-            build_batch_lists(hp, valid, G, FB, TL);
+            build_batch_lists(hp, valid, G, FB, TL, h->cfg.batch_narrow);
             tst = upload_lists(h, TL, D, FB);
             if (tst != DROT_OK) break;
             // alternating directions, as the solve runs them
             drot::BatchArgs At = A;
             At.odd = 1;
             drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(At);
+            if (TL.split) drot::drot_batched_narrow_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(At);
             e = cudaEventRecord(e0, h->stream);
             for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
                 At.odd = r & 1;
                 drot::drot_batched_step_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(At);
+                if (TL.split) drot::drot_batched_narrow_kernel<true><<<G, drot::kThreads, 0, h->stream>>>(At);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
@@ -1305,7 +1383,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
                 tst = fail(h, DROT_ERR_CUDA, "tuning launch failed: %s", cudaGetErrorString(e));
                 break;
             }
-            h->prof.kernel_launches += 4;
+            h->prof.kernel_launches += TL.split ? 8 : 4;
             if (ms < best) {
                 best = ms;
                 best_p = pi;
@@ -1322,6 +1400,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         for (int b = 0; b < B; ++b) {
             hp[b].K = batch_k(hp[b].n, thr);
             hp[b].T = (int)((hp[b].n + 128LL * hp[b].K - 1) / (128LL * hp[b].K));
+            hp[b].Tw = wide_tiles(hp[b].n, hp[b].K, hp[b].T);
         }
         DROT_CUDA(h, cudaMemcpyAsync(D.probs, hp.data(), sizeof(drot::BatchProb) * B, cudaMemcpyHostToDevice,
                                      h->stream));
@@ -1338,18 +1417,24 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         h->prof.kernel_launches += 1;
     }
     BatchLists L;
-    build_batch_lists(hp, valid, G, FB, L);
+    build_batch_lists(hp, valid, G, FB, L, h->cfg.batch_narrow);
     st = upload_lists(h, L, D, FB);
     if (st != DROT_OK) return st;
     drot::drot_batched_step_kernel<false><<<G, drot::kThreads, 0, h->stream>>>(A);
     DROT_CUDA(h, cudaGetLastError());
+    if (L.split) {
+        drot::drot_batched_narrow_kernel<false><<<G, drot::kThreads, 0, h->stream>>>(A);
+        DROT_CUDA(h, cudaGetLastError());
+        h->prof.kernel_launches += 1;
+    }
     drot::drot_batched_init_state_kernel<<<FB, drot::kFinishThreads, 0, h->stream>>>(A);
     DROT_CUDA(h, cudaGetLastError());
     h->prof.kernel_launches += 2;
 
-    // Graph replays of gi iterations over the active list.  gi follows the work still
-    // active (about 4 ms per replay, a power of 4 up to 256), so the replays stay long
-    // enough to hide the host round trip as problems converge; one graph per gi.
+    // Graph replays of gi iterations over the active lists.  gi follows the work still
+    // active (about 32 ms per replay, a power of 4 up to 256), so the replays stay long
+    // enough to hide the host round trip as problems converge; one graph per (gi, whether
+    // the narrow-tile kernel runs).
     std::vector<std::pair<int, cudaGraphExec_t>> graphs;
     auto release = [&]() {
         for (auto &g : graphs) cudaGraphExecDestroy(g.second);
@@ -1367,9 +1452,10 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         while (g < 256 && 4.0 * g <= want) g *= 4;
         return g;
     };
-    auto graph_for = [&](int g, cudaGraphExec_t *out) -> drot_status {
+    auto graph_for = [&](int g, bool split, cudaGraphExec_t *out) -> drot_status {
+        const int key = 2 * g + (split ? 1 : 0);
         for (auto &e : graphs)
-            if (e.first == g) {
+            if (e.first == key) {
                 *out = e.second;
                 return DROT_OK;
             }
@@ -1379,7 +1465,11 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         for (int it = 0; it < g && err == cudaSuccess; ++it) {
             drot::BatchArgs Ai = A;
             Ai.odd = it & 1;  // added to the parity word the host keeps between replays
+            Ai.narrow_next = split ? 1 : 0;
             err = launch_k(drot::drot_batched_step_kernel<true>, dim3(G), dim3(drot::kThreads), 0, h->stream, true, Ai);
+            if (err == cudaSuccess && split)
+                err = launch_k(drot::drot_batched_narrow_kernel<true>, dim3(G), dim3(drot::kThreads), 0, h->stream,
+                               true, Ai);
             if (err == cudaSuccess)
                 err = launch_k(drot::drot_batched_finish_kernel, dim3(FB), dim3(drot::kBatchFinishThreads), 0, h->stream,
                                true, A);
@@ -1395,7 +1485,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess)
             return fail(h, DROT_ERR_CUDA, "batched graph instantiate failed: %s", cudaGetErrorString(ie));
-        graphs.emplace_back(g, exec);
+        graphs.emplace_back(key, exec);
         *out = exec;
         return DROT_OK;
     };
@@ -1407,7 +1497,7 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
         for (long long r = 0; r < max_replays && !active.empty(); ++r) {
             const int gi = pick_gi(active);
             cudaGraphExec_t exec = nullptr;
-            st = graph_for(gi, &exec);
+            st = graph_for(gi, L.split, &exec);
             if (st != DROT_OK) {
                 release();
                 return st;
@@ -1428,12 +1518,12 @@ drot_status solve_batched_device(drot_handle *h, int B, const drot_problem *pr, 
                 return fail(h, DROT_ERR_CUDA, "batched replay failed: %s", cudaGetErrorString(e));
             }
             h->prof.graph_replays += 1;
-            h->prof.kernel_launches += 2LL * gi;
+            h->prof.kernel_launches += (L.split ? 3LL : 2LL) * gi;
             std::vector<int> still;
             for (int b : active)
                 if (h->h_bstat[b].done == drot::kRunning) still.push_back(b);
             if (still.size() != active.size() && !still.empty()) {
-                build_batch_lists(hp, still, G, FB, L);
+                build_batch_lists(hp, still, G, FB, L, h->cfg.batch_narrow);
                 st = upload_lists(h, L, D, FB);
                 if (st != DROT_OK) {
                     release();
@@ -1588,6 +1678,7 @@ void drot_config_default(drot_config *cfg) {
     cfg->persistent = 0;
     cfg->c_skip = 0;
     cfg->cluster = 0;
+    cfg->batch_narrow = 0;
 }
 
 drot_status drot_create(drot_handle **out, const drot_config *cfg) {

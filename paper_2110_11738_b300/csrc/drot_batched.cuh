@@ -8,7 +8,12 @@
 // segments of all active problems form one list (problem-major, then tile-major,
 // then row), the host cuts that list into one contiguous, cost-balanced range per
 // CTA, and each CTA walks its range segment by segment, taking the tile width of
-// the problem a segment belongs to.  The finish launch gives each active problem
+// the problem a segment belongs to.  Tiles with at most 256 valid columns (the narrow
+// last tile of a 512-column tiling, or every tile of a narrower tiling) form a second
+// list served by a second kernel, which packs two or four rows into one warp iteration
+// so that a narrow tile still moves up to 2 KB per array per memory round trip; it is a
+// separate kernel so that neither loop takes registers from the other, and its CTAs
+// start on the SMs the first kernel's CTAs leave.  The finish launch gives each active problem
 // its own group of blocks; the last block of a group closes that problem's
 // iteration.  Converged problems are dropped from the lists between graph replays
 // (and their segments skipped inside a replay), so the work of a launch shrinks as
@@ -36,6 +41,7 @@ struct BatchProb {
     double inv_n, inv_m;
     int K;                  // float4 chunks per lane (tile width 128 K)
     int T;                  // column tiles
+    int Tw;                 // tiles [0, Tw) are wide (> 256 valid columns), [Tw, T) narrow
     int fin_blocks;         // blocks of the finish launch serving this problem
     int pad;
 };
@@ -50,6 +56,12 @@ struct BatchArgs {
     const int* fin_local;      // [FB] index of the block within its problem's group
     const int* nactive;        // number of active problems (device, updated between replays)
     const int* parity;         // parity of the iterations already run (device, updated between replays)
+    // the narrow tiles' list, same layout (segments of tiles Tw .. T-1 of each problem that has any)
+    const int* active_n;
+    const long long* unit0_n;
+    const long long* wbound_n;
+    const int* nactive_n;
+    int narrow_next;           // 1: the narrow-tile kernel follows this wide-tile launch
     int warm;
     int serp;                  // 1: alternate the direction of the passes (as SegWalk does)
     int odd;                   // parity of this pass in its graph; backwards when serp and parity + odd is odd
@@ -77,8 +89,28 @@ __device__ __forceinline__ FinishArgs batch_finish_args(const BatchProb& P) {
     return F;
 }
 
-// Fused DR pass over every active problem (UPDATE = false: row/column sums of
-// X_0 only, used once at initialisation).
+// Warp-wide sums of four FP32 values per lane in a fixed order (a reduce-scatter
+// butterfly, six shuffles instead of four five-level trees): lane l returns the warp
+// total of value (l >> 3) & 3.
+__device__ __forceinline__ float warp_sum4_scatter_f32(const float (&v)[4]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+    float k2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = b4 ? v[2 + i] : v[i];
+        const float give = b4 ? v[i] : v[2 + i];
+        k2[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+    float k1 = (b3 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b3 ? k2[0] : k2[1], 8);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 4);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+    return k1;
+}
+
+// Fused DR pass over the wide tiles of every active problem (UPDATE = false: row/column
+// sums of X_0 only, used once at initialisation).
 template <bool UPDATE>
 __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArgs B) {
     constexpr int KMAX = 4;
@@ -88,6 +120,11 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
     __shared__ float s_phi[kPhiChunk];   // formed once per CTA (FP64 is scarce: see StepSmem)
 
     wait_for_predecessor();
+    // the narrow-tile kernel launched after this one may start its blocks now: it reads
+    // only what the finish before this kernel wrote, and waits for this grid before it ends
+    // (a finish launched next instead is not released early: its blocks would take the
+    // SMs this kernel frees and hold them waiting)
+    if (B.narrow_next) release_dependents();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const long long w0 = B.wbound[blockIdx.x];
@@ -256,6 +293,202 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
             __syncthreads();
         }
     }
+}
+
+// Rows of one narrow tile packed into warp iterations: a lane's four float4 slots serve
+// R = 4 >> lg rows of the group (slot kk: row kk >> lg, column chunk kk & (2^lg - 1)), lg = 0
+// for at most 128 valid columns, 1 for at most 256.
+constexpr int kNarrowCols = 256;
+
+// Fused DR pass over the narrow tiles of every active problem (UPDATE = false: sums of X_0).
+// Launched right after drot_batched_step_kernel as its programmatic dependent: it does not
+// wait for that kernel to begin (it reads only what the finish before both wrote, through
+// L2), and it waits for it before ending, so the finish launched after this kernel sees the
+// totals of both.
+template <bool UPDATE>
+__global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchArgs B) {
+    constexpr int KMAX = 4;
+    __shared__ double s_col[kWarps][kNarrowCols];
+    __shared__ double s_red[kWarps][2];
+    __shared__ float s_psi[kNarrowCols];
+    __shared__ float s_phi[kPhiChunk];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long w0 = B.wbound_n[blockIdx.x];
+    const long long w1 = B.wbound_n[blockIdx.x + 1];
+    const int nactive = __ldcg(B.nactive_n);
+    if (w0 < w1 && nactive > 0) {
+        const bool rev = B.serp != 0 && ((__ldcg(B.parity) + B.odd) & 1) != 0;
+        const long long wfirst = rev ? w1 - 1 : w0;
+        int lo = 0, hi = nactive - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.unit0_n[mid] <= wfirst) lo = mid;
+            else hi = mid - 1;
+        }
+        int ai = lo;
+        long long w = rev ? w1 : w0;
+        while (rev ? w > w0 : w < w1) {
+            if (rev) {
+                while (ai > 0 && w - 1 < B.unit0_n[ai]) --ai;
+            } else {
+                while (ai + 1 < nactive && w >= B.unit0_n[ai + 1]) ++ai;
+            }
+            const BatchProb& P = B.probs[B.active_n[ai]];
+            const long long base = B.unit0_n[ai];
+            const long long m = P.m, n = P.n, ld = P.ld;
+            const long long tl = ((rev ? w - 1 : w) - base) / m;
+            const long long seg_lo = rev ? max(w0, base + tl * m) : w;
+            const long long seg_hi = rev ? w : min(w1, base + (tl + 1) * m);
+            const long long i0 = seg_lo - base - tl * m, i1 = seg_hi - base - tl * m;
+            w = rev ? seg_lo : seg_hi;
+            if (__ldcg(&P.sc->done) != kRunning) continue;  // uniform: every thread reads the same flag
+
+            const int TW = 128 * P.K;
+            const long long col0 = (P.Tw + tl) * TW;
+            const long long wcols = min((long long)TW, n - col0);  // <= kNarrowCols
+            const int lg = wcols <= 128 ? 0 : 1;
+            const int cmask = (1 << lg) - 1;
+            const int R = KMAX >> lg;
+            const double cs = __ldcg(&P.sc->c);
+            const float rho = UPDATE ? (float)P.sc->rho : 0.f;
+
+            // every thread arrives here together (the previous segment ended with a barrier)
+            if (UPDATE) {
+                for (int x = threadIdx.x; x < wcols; x += kThreads)
+                    s_psi[x] = (float)((__ldcg(P.h + col0 + x) + cs) * P.inv_m);
+            }
+            for (int x = lane; x < kNarrowCols; x += 32) s_col[warp][x] = 0.0;
+            float psi[KMAX][4], cacc[KMAX][4];
+            float scx = 0.f, sd = 0.f;
+            double scx64 = 0.0, sd64 = 0.0;
+            int since_flush = 0;
+            const long long c_first = rev ? i1 : i0;
+            for (long long c = c_first; rev ? c > i0 : c < i1; c += rev ? -kPhiChunk : kPhiChunk) {
+            const long long r0 = rev ? max(i0, c - (long long)kPhiChunk) : c;
+            const long long r1 = rev ? c : min(i1, c + (long long)kPhiChunk);
+            if (UPDATE) {
+                if (c != c_first) __syncthreads();  // every warp is done with the previous chunk's phi
+                for (long long r = r0 + threadIdx.x; r < r1; r += kThreads)
+                    s_phi[r - r0] = (float)((__ldcg(P.g + r) + cs) * P.inv_n);
+            }
+            __syncthreads();
+            if (c == c_first) {
+#pragma unroll
+                for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int x = (kk & cmask) * 128 + lane * 4 + e;
+                        psi[kk][e] = (UPDATE && x < wcols) ? s_psi[x] : 0.f;
+                        cacc[kk][e] = 0.f;
+                    }
+            }
+            // slot kk holds the row at chunk offset q + dstep (kk >> lg), valid while in [0, nr)
+            const long long nr = r1 - r0;
+            const long long dstep = rev ? -(long long)kWarps : (long long)kWarps;
+            for (long long q = rev ? nr - 1 - warp : warp; (unsigned long long)q < (unsigned long long)nr;
+                 q += R * dstep) {
+                float4 xv[KMAX], cv[KMAX];
+#pragma unroll
+                for (int kk = 0; kk < KMAX; ++kk) {
+                    const long long rq = q + dstep * (kk >> lg);
+                    const long long jl = (kk & cmask) * 128 + lane * 4;
+                    if ((unsigned long long)rq < (unsigned long long)nr && jl < wcols) {
+                        const long long off = (r0 + rq) * ld + col0 + jl;
+                        xv[kk] = *reinterpret_cast<const float4*>(P.X + off);
+                        if (UPDATE) cv[kk] = ld_stream_ro(P.C + off);
+                    }
+                }
+                float rsk[KMAX];
+#pragma unroll
+                for (int kk = 0; kk < KMAX; ++kk) {
+                    rsk[kk] = 0.f;
+                    const long long rq = q + dstep * (kk >> lg);
+                    const long long jl = (kk & cmask) * 128 + lane * 4;
+                    if ((unsigned long long)rq < (unsigned long long)nr && jl < wcols) {
+                        const float phi = UPDATE ? s_phi[rq] : 0.f;
+                        float xs[4] = {xv[kk].x, xv[kk].y, xv[kk].z, xv[kk].w};
+                        float cc[4] = {0.f, 0.f, 0.f, 0.f};
+                        if (UPDATE) { cc[0] = cv[kk].x; cc[1] = cv[kk].y; cc[2] = cv[kk].z; cc[3] = cv[kk].w; }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (jl + e < wcols) {
+                                float xn = xs[e];
+                                if (UPDATE) {
+                                    const float d = fmaf(-rho, cc[e], phi + psi[kk][e]);
+                                    xn = fmaxf(xs[e] + d, 0.f);
+                                    scx = fmaf(cc[e], xn, scx);
+                                    const float dp = fmaxf(d, 0.f);
+                                    sd = fmaf(dp, dp, sd);
+                                    xs[e] = xn;
+                                }
+                                rsk[kk] += xn;
+                                cacc[kk][e] += xn;
+                            }
+                        }
+                        if (UPDATE) {
+                            float* dst = P.X + (r0 + rq) * ld + col0 + jl;
+                            if (jl + 3 < wcols) {
+                                *reinterpret_cast<float4*>(dst) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    if (jl + e < wcols) dst[e] = xs[e];
+                            }
+                        }
+                    }
+                }
+                // lanes 8g .. 8g+7 receive the warp total of slot g; a row owns 2^lg slots
+                float tot = warp_sum4_scatter_f32(rsk);
+                if (lg == 1) tot += __shfl_xor_sync(0xffffffffu, tot, 8);
+                const long long rq = q + dstep * (lane >> (3 + lg));
+                if ((lane & ((8 << lg) - 1)) == 0 && (unsigned long long)rq < (unsigned long long)nr)
+                    atomicAdd(P.u + r0 + rq, (double)tot);
+                if (++since_flush == kFlushRows) {
+#pragma unroll
+                    for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            s_col[warp][(kk & cmask) * 128 + lane * 4 + e] += (double)cacc[kk][e];
+                            cacc[kk][e] = 0.f;
+                        }
+                    scx64 += (double)scx;
+                    sd64 += (double)sd;
+                    scx = 0.f;
+                    sd = 0.f;
+                    since_flush = 0;
+                }
+            }
+            }  // row chunks
+#pragma unroll
+            for (int kk = 0; kk < KMAX; ++kk)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) s_col[warp][(kk & cmask) * 128 + lane * 4 + e] += (double)cacc[kk][e];
+            scx64 += (double)scx;
+            sd64 += (double)sd;
+            __syncthreads();
+            for (int x = threadIdx.x; x < wcols; x += kThreads) {
+                double v = 0.0;
+#pragma unroll
+                for (int wv = 0; wv < kWarps; ++wv) v += s_col[wv][x];
+                atomicAdd(P.v + col0 + x, v);
+            }
+            if (UPDATE) {
+                double v2[2] = {scx64, sd64};
+                block_sum_f64<2, kThreads>(v2, s_red);  // ends with a block barrier
+                if (threadIdx.x == 0) {
+                    atomicAdd(acc_at(P.acc, 0), v2[0]);
+                    atomicAdd(acc_at(P.acc, 1), v2[1]);
+                }
+            } else {
+                __syncthreads();
+            }
+        }
+    }
+    // end only after the wide-tile pass launched before this kernel (a no-op when this
+    // kernel was not launched as a programmatic dependent)
+    wait_for_predecessor();
 }
 
 // Steps 5-8 and the stopping test of every active problem (one block group each).

@@ -55,7 +55,8 @@ class DrotConfig(ctypes.Structure):
                 ("grid_ctas", ctypes.c_int), ("profile", ctypes.c_int), ("step_variant", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("c_skip", ctypes.c_int), ("cluster", ctypes.c_int), ("trace", ctypes.c_void_p),
-                ("trace_len", ctypes.c_int64), ("wait_limit", ctypes.c_int64), ("serpentine", ctypes.c_int)]
+                ("trace_len", ctypes.c_int64), ("wait_limit", ctypes.c_int64), ("serpentine", ctypes.c_int),
+                ("batch_narrow", ctypes.c_int)]
 
 
 class DrotResult(ctypes.Structure):
@@ -169,12 +170,15 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
                 rho0: float = 2.0, graph_iters: int = 0, tile_k: int = 0, grid_ctas: int = 0,
                 profile: bool = False, step_variant: int = 0, deterministic: bool = False,
                 autotune: bool = False, persistent: bool = False, c_skip: bool = False,
-                cluster: int = 0, trace=None, wait_limit: int = 0, serpentine: int = 0) -> int:
+                cluster: int = 0, trace=None, wait_limit: int = 0, serpentine: int = 0,
+                batch_narrow: int = 0) -> int:
     """Create a solver handle; returns the opaque handle as an int.  ``trace``: optional float64
     CUDA tensor of 2 * L entries that receives <C, X_k> and the l1 residual of iterations 1 .. L
     of every solve (the caller keeps it alive while the handle is used).  ``serpentine``: 1 or 0
     (default) alternates the direction of the fused-step passes so that each starts on what the
-    previous one left in L2; -1 runs every pass forwards."""
+    previous one left in L2; -1 runs every pass forwards.  ``batch_narrow`` (batched solves): 1
+    always, -1 never, 0 (default) automatically sends tiles of at most 256 columns to the kernel
+    that packs rows."""
     lib = load()
     cfg = DrotConfig()
     lib.drot_config_default(ctypes.byref(cfg))
@@ -194,6 +198,7 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
     cfg.cluster = int(cluster)
     cfg.wait_limit = int(wait_limit)
     cfg.serpentine = int(serpentine)
+    cfg.batch_narrow = int(batch_narrow)
     if trace is not None:
         cfg.trace = _ptr(trace)
         cfg.trace_len = int(trace.numel()) // 2

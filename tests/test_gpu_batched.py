@@ -38,9 +38,15 @@ def _shapes():
 # default: alternating pass directions within each graph; graph_iters=1: one iteration per
 # replay, so the direction comes from the parity word the host rewrites between replays;
 # serpentine=-1: every pass forwards; tile_k 1 and 2: 128- and 256-column tiles for every
-# problem (the step kernel's narrower tile widths, which the tile-policy autotuner may pick)
+# problem (the step kernel's narrower tile widths, which the tile-policy autotuner may pick);
+# batch_narrow=1: tiles of at most 256 columns in the kernel that packs rows ((517, 63), (200, 1029),
+# (33, 4100) four rows per warp iteration, (1000, 130) two; with tile_k 1 or 2 every tile),
+# batch_narrow=-1: every tile in the wide-tile kernel
 @pytest.mark.parametrize("cfg", [{}, {"graph_iters": 1}, {"serpentine": -1}, {"tile_k": 1}, {"tile_k": 2},
-                                 {"tile_k": 1, "serpentine": -1}])
+                                 {"tile_k": 1, "serpentine": -1}, {"batch_narrow": 1},
+                                 {"batch_narrow": 1, "graph_iters": 1}, {"batch_narrow": 1, "serpentine": -1},
+                                 {"batch_narrow": 1, "tile_k": 1}, {"batch_narrow": 1, "tile_k": 2},
+                                 {"batch_narrow": -1}])
 def test_batched_step_parity_with_oracle(cfg):
     probs, starts, specs = [], [], []
     for b, (m, n) in enumerate(_shapes()):
@@ -64,11 +70,12 @@ def test_batched_step_parity_with_oracle(cfg):
         assert abs(r["primal_obj"] - h[oracle.PRIMAL]) <= 1e-5 * abs(h[oracle.PRIMAL]) + 1e-9
 
 
-def test_batched_solves_match_single_solves():
+@pytest.mark.parametrize("narrow", [0, 1])
+def test_batched_solves_match_single_solves(narrow):
     specs = [workloads.make_problem("plain_256", seed=s, m=m, n=n)
              for s, (m, n) in enumerate([(40, 60), (96, 80), (61, 190), (128, 128), (20, 300)])]
     probs = [_dev_problem(pr) for pr in specs]
-    with drot.Solver(device=0) as s:
+    with drot.Solver(device=0, batch_narrow=narrow) as s:
         res = s.solve_batched(probs, tol=1e-6, max_iter=2_000_000)
         for pr, P, r in zip(specs, probs, res):
             assert r["status"] == drot.DROT_OK, r
@@ -98,13 +105,14 @@ def test_batched_reports_per_problem_status():
     assert res[0]["primal_obj"] == pytest.approx(res[2]["primal_obj"], rel=1e-6)
 
 
-def test_batched_uneven_config_subset_iteration_cap():
+@pytest.mark.parametrize("narrow", [0, 1])
+def test_batched_uneven_config_subset_iteration_cap(narrow):
     # 24 problems drawn like the 512-problem workload (m, n uniform in [64, 2048], shifted
     # clouds, Dirichlet marginals), a fixed iteration budget: every problem must agree with
     # its own single solve after the same number of iterations
     specs = workloads.make_batch(B=24, seed=3)
     probs = [_dev_problem(pr) for pr in specs]
-    with drot.Solver(device=0) as s:
+    with drot.Solver(device=0, batch_narrow=narrow) as s:
         res = s.solve_batched(probs, tol=-1.0, max_iter=200)
         for pr, P, r in zip(specs[:6], probs[:6], res[:6]):
             assert r["iters"] == 200

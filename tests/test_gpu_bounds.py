@@ -135,7 +135,8 @@ def test_f64_solve_stays_inside_its_buffers(m, n):
     _check_against_oracle(pr, bufs, out, X0, mu0, nu0, k, C64=C64, f64=True)
 
 
-def test_batched_solve_stays_inside_every_problems_buffers():
+@pytest.mark.parametrize("narrow", [-1, 1])  # narrow tiles in the wide-tile kernel / in their own packed kernel
+def test_batched_solve_stays_inside_every_problems_buffers(narrow):
     k = 4
     cases = []
     for b, (m, n) in enumerate([(3, 7), (130, 257), (1, 1), (257, 1031), (64, 2048)]):
@@ -144,7 +145,7 @@ def test_batched_solve_stays_inside_every_problems_buffers():
         cases.append((pr, X0, mu0, nu0, _guarded_problem(pr, X0, mu0, nu0)))
     probs = [dict(C=g["C"].t, X=g["X"].t, p=g["p"].t, q=g["q"].t, mu=g["mu"].t, nu=g["nu"].t, rho=pr.rho)
              for pr, _, _, _, g in cases]
-    with drot.Solver(device=0) as s:
+    with drot.Solver(device=0, batch_narrow=narrow) as s:
         res = s.solve_batched(probs, tol=-1.0, max_iter=k, warm=True, check=False)
     for (pr, X0, mu0, nu0, g), r in zip(cases, res):
         _check_guards(g)
