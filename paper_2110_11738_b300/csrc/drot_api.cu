@@ -402,9 +402,18 @@ void make_plan(const drot_handle *h, long long m, long long n, Plan &P, int forc
             }
     }
     if (K != 1 && K != 2 && K != 4) {
+        // the widest tile the rows fill ...
         if (n >= 1536) K = 4;
         else if (n >= 384) K = 2;
         else K = 1;
+        // ... but a plan of a few million entries sits in L2, where a pass is bound by the
+        // latency of each warp's row round trips rather than by bandwidth, and narrower tiles
+        // put more row segments in flight.  Measured per iteration on B300 (128- / 256- /
+        // 512-column tiles): 1024^2 14.7 / 15.8 / 20.0 µs, 1536^2 17.7 / 17.6 / 21.5,
+        // 2048^2 20.6 / 20.0 / 22.8, 700 x 5000 20.4 / 19.9 / 22.7; 3072^2 34.2 / 30.0 / 28.6
+        const double entries = (double)m * (double)n;
+        if (entries <= 1.5e6) K = 1;
+        else if (entries <= 6.0e6) K = std::min(K, 2);
     }
     P.K = K;
     P.TW = 128 * K;

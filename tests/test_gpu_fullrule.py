@@ -62,21 +62,26 @@ def test_every_golden_case_is_committed():
     assert {"gauss_384x512", "gauss_768x1024"} <= names, names
 
 
-@pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(g)[9:-5] for g in GOLDEN])
-def test_full_rule_solve_matches_the_oracle(path):
+CASES = [(g, k) for g in GOLDEN for k in ((0, 4) if "1536x2048" in g else (0,))]
+
+
+@pytest.mark.parametrize("path,tile_k", CASES, ids=[f"{os.path.basename(g)[9:-5]}-k{k}" for g, k in CASES])
+def test_full_rule_solve_matches_the_oracle(path, tile_k):
+    """tile_k 0: the autotuned plan; 4: the 512-column tiles of the full-size workloads."""
     gold = json.load(open(path))
     assert gold["status"] == oracle.STATUS_CONVERGED
     pr = workloads.make_problem(gold["workload"], seed=gold["seed"], m=gold["m"], n=gold["n"])
     assert _input_hash(pr.C, pr.p, pr.q) == gold["input_sha256"]
     C, p, q, X, mu, nu = _gpu_buffers(pr)
-    with drot.Solver(device=0, autotune=True) as s:
+    with drot.Solver(device=0, autotune=True, tile_k=tile_k) as s:
         out = s.solve(C, p, q, rho=pr.rho, tol=gold["tol"], max_iter=4_000_000, X=X, mu=mu, nu=nu)
         plan = s.profile()
     assert out["status"] == drot.DROT_OK, out
     if pr.n >= 1536:
-        # the full-size kernel path: every CTA of the fused step, several 512-column tiles
+        # the streaming path on every CTA of the fused step, several column tiles
         assert plan["grid_ctas"] >= 2 * torch.cuda.get_device_properties(0).multi_processor_count
-        assert plan["col_tiles"] >= 4 and plan["tile_k"] == 4 and plan["step_variant"] in (1, 2, 3)
+        assert plan["col_tiles"] >= 4 and plan["step_variant"] in (1, 2, 3)
+        assert tile_k == 0 or plan["tile_k"] == tile_k
     obj = gold["primal"]
     assert abs(out["primal_obj"] - obj) <= 1e-5 * abs(obj), (out["primal_obj"], obj)
     assert abs(out["dual_obj"] - gold["dual"]) <= 1e-5 * abs(obj) + 2 * gold["tol"]
