@@ -59,7 +59,7 @@ def _gpu_buffers(pr):
 
 def test_every_golden_case_is_committed():
     names = {os.path.basename(g)[len("fullrule_"):-len(".json")] for g in GOLDEN}
-    assert {"gauss_384x512", "gauss_768x1024"} <= names, names
+    assert {"gauss_384x512", "gauss_768x1024", "gauss_1536x2048"} <= names, names
 
 
 CASES = [(g, k) for g in GOLDEN for k in ((0, 4) if "1536x2048" in g else (0,))]
