@@ -80,8 +80,8 @@ constexpr double kRowTripCols = 1536.0;
 constexpr double kTileSwitchCols = 64.0 * (512.0 + kRowTripCols);
 
 // Rows the batched narrow-tile kernel packs into one warp iteration for a tile of w valid
-// columns (w <= 256): four up to 128 columns, two up to 256.
-inline int packed_rows(long long w) { return w <= 128 ? 4 : (w <= 256 ? 2 : 1); }
+// columns (w <= 256): eight up to 128 columns, four up to 256.
+inline int packed_rows(long long w) { return w <= 128 ? 8 : (w <= 256 ? 4 : 1); }
 
 struct SegCost {
     long long m, T, TW, last_w;

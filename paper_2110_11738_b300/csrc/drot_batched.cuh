@@ -10,10 +10,14 @@
 // CTA, and each CTA walks its range segment by segment, taking the tile width of
 // the problem a segment belongs to.  Tiles with at most 256 valid columns (the narrow
 // last tile of a 512-column tiling, or every tile of a narrower tiling) form a second
-// list served by a second kernel, which packs two or four rows into one warp iteration
-// so that a narrow tile still moves up to 2 KB per array per memory round trip; it is a
+// list served by a second kernel, which packs four or eight rows into one warp iteration
+// so that a narrow tile still moves up to 4 KB per array per memory round trip; it is a
 // separate kernel so that neither loop takes registers from the other, and its CTAs
-// start on the SMs the first kernel's CTAs leave.  The finish launch gives each active problem
+// start on the SMs the first kernel's CTAs leave.  Both kernels have a warp prefetch the
+// rows of its next iteration into L2 while its current loads are in flight: a warp then
+// keeps two iterations' bytes in flight with one iteration's registers, which is what a
+// ragged or narrow tile (fewer bytes per round trip) and the start of every segment need.
+// The finish launch gives each active problem
 // its own group of blocks; the last block of a group closes that problem's
 // iteration.  Converged problems are dropped from the lists between graph replays
 // (and their segments skipped inside a replay), so the work of a launch shrinks as
@@ -87,26 +91,6 @@ __device__ __forceinline__ FinishArgs batch_finish_args(const BatchProb& P) {
     F.inv_m = P.inv_m;
     F.inv_mn = 1.0 / (double)(P.m + P.n);
     return F;
-}
-
-// Warp-wide sums of four FP32 values per lane in a fixed order (a reduce-scatter
-// butterfly, six shuffles instead of four five-level trees): lane l returns the warp
-// total of value (l >> 3) & 3.
-__device__ __forceinline__ float warp_sum4_scatter_f32(const float (&v)[4]) {
-    const int lane = threadIdx.x & 31;
-    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
-    float k2[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float keep = b4 ? v[2 + i] : v[i];
-        const float give = b4 ? v[i] : v[2 + i];
-        k2[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
-    }
-    float k1 = (b3 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b3 ? k2[0] : k2[1], 8);
-    k1 += __shfl_xor_sync(0xffffffffu, k1, 4);
-    k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
-    k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
-    return k1;
 }
 
 // Fused DR pass over the wide tiles of every active problem (UPDATE = false: row/column
@@ -213,6 +197,17 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
                     if (UPDATE) cv[kk] = ld_stream_ro(P.C + rowoff + kk * 128);
                 }
             }
+            if (UPDATE) {
+                // the warp's next row of this chunk into L2 (lanes 0-15: X, 16-31: C; one 128-byte
+                // line each): its loads then find it there, so a warp has two rows in flight
+                // without holding a second row's registers
+                const long long inext = rev ? i - kWarps : i + kWarps;
+                const int line = lane & 15;
+                if (inext >= r0 && inext < r1 && line * 32 < TW && col0 + line * 32 < n) {
+                    const float* pf = (lane < 16 ? P.X : P.C) + inext * ld + col0 + line * 32;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
+                }
+            }
             float rs = 0.f;
 #pragma unroll
             for (int kk = 0; kk < KMAX; ++kk) {
@@ -295,10 +290,46 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_step_kernel(BatchArg
     }
 }
 
-// Rows of one narrow tile packed into warp iterations: a lane's four float4 slots serve
-// R = 4 >> lg rows of the group (slot kk: row kk >> lg, column chunk kk & (2^lg - 1)), lg = 0
-// for at most 128 valid columns, 1 for at most 256.
+// Warp-wide sums of eight FP32 values per lane in a fixed order (a reduce-scatter
+// butterfly, seven shuffles instead of eight five-level trees): lane l returns the warp
+// total of value (l >> 2) & 7.
+__device__ __forceinline__ float warp_sum8_scatter_f32(const float (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+    float k4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float keep = b4 ? v[4 + i] : v[i];
+        const float give = b4 ? v[i] : v[4 + i];
+        k4[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+    float k2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = b3 ? k4[2 + i] : k4[i];
+        const float give = b3 ? k4[i] : k4[2 + i];
+        k2[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    float k1 = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? k2[0] : k2[1], 4);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
+    k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+    return k1;
+}
+
+// Rows of one narrow tile packed into warp iterations: a lane's kNarrowSlots float4 slots
+// serve R = kNarrowSlots >> lg rows of the group (slot kk: row kk >> lg, column chunk
+// kk & (2^lg - 1)), lg = 0 for at most 128 valid columns, 1 for at most 256.  A warp
+// iteration thus moves up to 4 KB of X and as much of C (eight rows of 128 columns, or four
+// of 256).  Slot kk touches the columns of chunk kk & 1 when
+// lg = 1 and of chunk 0 when lg = 0, so a lane keeps psi and its FP32 column partials for
+// two chunks (indexed kk & 1) whatever the number of slots; with lg = 0 both halves hold
+// chunk 0 and are added together when they are promoted to FP64.
 constexpr int kNarrowCols = 256;
+constexpr int kNarrowSlots = 8;
+// warp iterations between FP32 -> FP64 promotions: every column partial then holds
+// kFlushRows rows, as in the wide-tile kernel (each half takes four rows per iteration)
+constexpr int kNarrowFlushIters = kFlushRows / (kNarrowSlots / 2);
+static_assert(kNarrowFlushIters * (kNarrowSlots / 2) == kFlushRows, "flush interval");
 
 // Fused DR pass over the narrow tiles of every active problem (UPDATE = false: sums of X_0).
 // Launched right after drot_batched_step_kernel as its programmatic dependent: it does not
@@ -307,7 +338,7 @@ constexpr int kNarrowCols = 256;
 // totals of both.
 template <bool UPDATE>
 __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchArgs B) {
-    constexpr int KMAX = 4;
+    constexpr int S = kNarrowSlots;
     __shared__ double s_col[kWarps][kNarrowCols];
     __shared__ double s_red[kWarps][2];
     __shared__ float s_psi[kNarrowCols];
@@ -347,10 +378,10 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchA
 
             const int TW = 128 * P.K;
             const long long col0 = (P.Tw + tl) * TW;
-            const long long wcols = min((long long)TW, n - col0);  // <= kNarrowCols
+            const int wcols = (int)min((long long)TW, n - col0);  // <= kNarrowCols
             const int lg = wcols <= 128 ? 0 : 1;
             const int cmask = (1 << lg) - 1;
-            const int R = KMAX >> lg;
+            const int R = S >> lg;
             const double cs = __ldcg(&P.sc->c);
             const float rho = UPDATE ? (float)P.sc->rho : 0.f;
 
@@ -360,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchA
                     s_psi[x] = (float)((__ldcg(P.h + col0 + x) + cs) * P.inv_m);
             }
             for (int x = lane; x < kNarrowCols; x += 32) s_col[warp][x] = 0.0;
-            float psi[KMAX][4], cacc[KMAX][4];
+            float psi[2][4], cacc[2][4];
             float scx = 0.f, sd = 0.f;
             double scx64 = 0.0, sd64 = 0.0;
             int since_flush = 0;
@@ -376,37 +407,54 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchA
             __syncthreads();
             if (c == c_first) {
 #pragma unroll
-                for (int kk = 0; kk < KMAX; ++kk)
+                for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int x = (kk & cmask) * 128 + lane * 4 + e;
-                        psi[kk][e] = (UPDATE && x < wcols) ? s_psi[x] : 0.f;
-                        cacc[kk][e] = 0.f;
+                        const int x = (hh & cmask) * 128 + lane * 4 + e;
+                        psi[hh][e] = (UPDATE && x < wcols) ? s_psi[x] : 0.f;
+                        cacc[hh][e] = 0.f;
                     }
             }
             // slot kk holds the row at chunk offset q + dstep (kk >> lg), valid while in [0, nr)
-            const long long nr = r1 - r0;
-            const long long dstep = rev ? -(long long)kWarps : (long long)kWarps;
-            for (long long q = rev ? nr - 1 - warp : warp; (unsigned long long)q < (unsigned long long)nr;
-                 q += R * dstep) {
-                float4 xv[KMAX], cv[KMAX];
+            const int nr = (int)(r1 - r0);
+            const int dstep = rev ? -kWarps : kWarps;
+            float* const Xc = P.X + r0 * ld + col0;
+            const float* const Cc = P.C + r0 * ld + col0;
+            for (int q = rev ? nr - 1 - warp : warp; (unsigned)q < (unsigned)nr; q += R * dstep) {
+                float4 xv[S], cv[S];
 #pragma unroll
-                for (int kk = 0; kk < KMAX; ++kk) {
-                    const long long rq = q + dstep * (kk >> lg);
-                    const long long jl = (kk & cmask) * 128 + lane * 4;
-                    if ((unsigned long long)rq < (unsigned long long)nr && jl < wcols) {
-                        const long long off = (r0 + rq) * ld + col0 + jl;
-                        xv[kk] = *reinterpret_cast<const float4*>(P.X + off);
-                        if (UPDATE) cv[kk] = ld_stream_ro(P.C + off);
+                for (int kk = 0; kk < S; ++kk) {
+                    const int rq = q + dstep * (kk >> lg);
+                    const int jl = (kk & cmask) * 128 + lane * 4;
+                    if ((unsigned)rq < (unsigned)nr && jl < wcols) {
+                        const long long off = (long long)rq * ld + jl;
+                        xv[kk] = *reinterpret_cast<const float4*>(Xc + off);
+                        if (UPDATE) cv[kk] = ld_stream_ro(Cc + off);
                     }
                 }
-                float rsk[KMAX];
+                if (UPDATE) {
+                    // the rows of the warp's next iteration into L2 (R rows x 2^(lg+2) lines x 2 arrays = 64)
+                    const int qn = q + R * dstep;
+                    const int lines = 4 << lg;
 #pragma unroll
-                for (int kk = 0; kk < KMAX; ++kk) {
+                    for (int t0 = 0; t0 < 64; t0 += 32) {
+                        const int t = t0 + lane;
+                        const int arr = t >> 5, rem = t & 31;
+                        const int rq = qn + dstep * (rem >> (2 + lg));
+                        const int line = rem & (lines - 1);
+                        if ((unsigned)rq < (unsigned)nr && line * 32 < wcols) {
+                            const float* pf = (arr ? Cc : Xc) + (long long)rq * ld + line * 32;
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
+                        }
+                    }
+                }
+                float rsk[S];
+#pragma unroll
+                for (int kk = 0; kk < S; ++kk) {
                     rsk[kk] = 0.f;
-                    const long long rq = q + dstep * (kk >> lg);
-                    const long long jl = (kk & cmask) * 128 + lane * 4;
-                    if ((unsigned long long)rq < (unsigned long long)nr && jl < wcols) {
+                    const int rq = q + dstep * (kk >> lg);
+                    const int jl = (kk & cmask) * 128 + lane * 4;
+                    if ((unsigned)rq < (unsigned)nr && jl < wcols) {
                         const float phi = UPDATE ? s_phi[rq] : 0.f;
                         float xs[4] = {xv[kk].x, xv[kk].y, xv[kk].z, xv[kk].w};
                         float cc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -416,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchA
                             if (jl + e < wcols) {
                                 float xn = xs[e];
                                 if (UPDATE) {
-                                    const float d = fmaf(-rho, cc[e], phi + psi[kk][e]);
+                                    const float d = fmaf(-rho, cc[e], phi + psi[kk & 1][e]);
                                     xn = fmaxf(xs[e] + d, 0.f);
                                     scx = fmaf(cc[e], xn, scx);
                                     const float dp = fmaxf(d, 0.f);
@@ -424,11 +472,11 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchA
                                     xs[e] = xn;
                                 }
                                 rsk[kk] += xn;
-                                cacc[kk][e] += xn;
+                                cacc[kk & 1][e] += xn;
                             }
                         }
                         if (UPDATE) {
-                            float* dst = P.X + (r0 + rq) * ld + col0 + jl;
+                            float* dst = Xc + (long long)rq * ld + jl;
                             if (jl + 3 < wcols) {
                                 *reinterpret_cast<float4*>(dst) = make_float4(xs[0], xs[1], xs[2], xs[3]);
                             } else {
@@ -439,20 +487,24 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchA
                         }
                     }
                 }
-                // lanes 8g .. 8g+7 receive the warp total of slot g; a row owns 2^lg slots
-                float tot = warp_sum4_scatter_f32(rsk);
-                if (lg == 1) tot += __shfl_xor_sync(0xffffffffu, tot, 8);
-                const long long rq = q + dstep * (lane >> (3 + lg));
-                if ((lane & ((8 << lg) - 1)) == 0 && (unsigned long long)rq < (unsigned long long)nr)
+                // lanes 4g .. 4g+3 receive the warp total of slot g; a row owns 2^lg slots
+                float tot = warp_sum8_scatter_f32(rsk);
+                if (lg == 1) tot += __shfl_xor_sync(0xffffffffu, tot, 4);
+                const int rq = q + dstep * (lane >> (2 + lg));
+                if ((lane & ((4 << lg) - 1)) == 0 && (unsigned)rq < (unsigned)nr)
                     atomicAdd(P.u + r0 + rq, (double)tot);
-                if (++since_flush == kFlushRows) {
+                if (++since_flush == kNarrowFlushIters) {
 #pragma unroll
-                    for (int kk = 0; kk < KMAX; ++kk)
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            s_col[warp][(kk & cmask) * 128 + lane * 4 + e] += (double)cacc[kk][e];
-                            cacc[kk][e] = 0.f;
+                    for (int e = 0; e < 4; ++e) {
+                        if (lg == 0) {
+                            s_col[warp][lane * 4 + e] += (double)cacc[0][e] + (double)cacc[1][e];
+                        } else {
+                            s_col[warp][lane * 4 + e] += (double)cacc[0][e];
+                            s_col[warp][128 + lane * 4 + e] += (double)cacc[1][e];
                         }
+                        cacc[0][e] = 0.f;
+                        cacc[1][e] = 0.f;
+                    }
                     scx64 += (double)scx;
                     sd64 += (double)sd;
                     scx = 0.f;
@@ -462,9 +514,14 @@ __global__ void __launch_bounds__(kThreads, 2) drot_batched_narrow_kernel(BatchA
             }
             }  // row chunks
 #pragma unroll
-            for (int kk = 0; kk < KMAX; ++kk)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) s_col[warp][(kk & cmask) * 128 + lane * 4 + e] += (double)cacc[kk][e];
+            for (int e = 0; e < 4; ++e) {
+                if (lg == 0) {
+                    s_col[warp][lane * 4 + e] += (double)cacc[0][e] + (double)cacc[1][e];
+                } else {
+                    s_col[warp][lane * 4 + e] += (double)cacc[0][e];
+                    s_col[warp][128 + lane * 4 + e] += (double)cacc[1][e];
+                }
+            }
             scx64 += (double)scx;
             sd64 += (double)sd;
             __syncthreads();

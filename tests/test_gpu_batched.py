@@ -32,7 +32,7 @@ def _dev_problem(pr, X0=None, mu0=None, nu0=None):
 
 
 def _shapes():
-    return [(1, 1), (3, 7), (64, 2048), (517, 63), (200, 1029), (1000, 130), (33, 4100), (257, 257)]
+    return [(1, 1), (3, 7), (64, 2048), (517, 63), (200, 1029), (1000, 130), (33, 4100), (257, 257), (301, 700)]
 
 
 # default: alternating pass directions within each graph; graph_iters=1: one iteration per
@@ -40,7 +40,8 @@ def _shapes():
 # serpentine=-1: every pass forwards; tile_k 1 and 2: 128- and 256-column tiles for every
 # problem (the step kernel's narrower tile widths, which the tile-policy autotuner may pick);
 # batch_narrow=1: tiles of at most 256 columns in the kernel that packs rows ((517, 63), (200, 1029),
-# (33, 4100) four rows per warp iteration, (1000, 130) two; with tile_k 1 or 2 every tile),
+# (33, 4100) eight rows per warp iteration, (1000, 130) and (301, 700) four; with tile_k 1 or 2 every
+# tile),
 # batch_narrow=-1: every tile in the wide-tile kernel
 @pytest.mark.parametrize("cfg", [{}, {"graph_iters": 1}, {"serpentine": -1}, {"tile_k": 1}, {"tile_k": 2},
                                  {"tile_k": 1, "serpentine": -1}, {"batch_narrow": 1},

@@ -139,7 +139,7 @@ def test_f64_solve_stays_inside_its_buffers(m, n):
 def test_batched_solve_stays_inside_every_problems_buffers(narrow):
     k = 4
     cases = []
-    for b, (m, n) in enumerate([(3, 7), (130, 257), (1, 1), (257, 1031), (64, 2048)]):
+    for b, (m, n) in enumerate([(3, 7), (130, 257), (1, 1), (257, 1031), (64, 2048), (301, 700)]):
         pr = workloads.make_problem("plain_8192x6144", seed=900 + b, m=m, n=n)
         X0, mu0, nu0 = workloads.random_start(m, n, seed=950 + b)
         cases.append((pr, X0, mu0, nu0, _guarded_problem(pr, X0, mu0, nu0)))
