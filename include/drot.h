@@ -274,7 +274,10 @@ drot_status drot_solve_static(int64_t m, int64_t n, const float *C, int64_t ld, 
  * DROT_MLP_PARAMS floats: W1[256x64] b1[256] W2[256x256] b2[256] W3[256x256] b3[256] W4[256] b4[1],
  * weights row-major [out x in]) with BF16 copies for the matrix products, BF16 activations,
  * FP32 accumulation, Adam updates.  Feature rows are BF16, DROT_MLP_FEATURES wide; see
- * drot_mlp_features for their content.  All buffers are device memory of the network's device. */
+ * drot_mlp_features for their content.  All buffers are device memory of the network's device.
+ * The matrix products run on the tcgen05 tensor cores (operands staged by TMA, accumulators in
+ * tensor memory); their waits are bounded, and a product that gave up makes drot_mlp_forward,
+ * drot_mlp_train_step and drot_mlp_warm_start return DROT_ERR_TIMEOUT. */
 #define DROT_MLP_FEATURES 64
 #define DROT_MLP_WIDTH 256
 #define DROT_MLP_PARAMS (256 * 64 + 256 + 2 * (256 * 256 + 256) + 256 + 1)

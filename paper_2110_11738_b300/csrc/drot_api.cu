@@ -2077,9 +2077,14 @@ struct drot_mlp {
     int device = 0;
     cudaStream_t stream = nullptr;
     float *w = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;  // DROT_MLP_PARAMS each
-    drot::mlp::bf16 *wb = nullptr;  // BF16 copies of W1, W2, W3
+    drot::mlp::bf16 *wb = nullptr;   // BF16 copies of W1, W2, W3
+    drot::mlp::bf16 *wbT = nullptr;  // BF16 copies of W2^T, W3^T (the backward pass's B operands)
+    int *err = nullptr;              // set by a tensor-core product whose wait gave up
     long long rows_cap = 0;
     drot::mlp::bf16 *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *D = nullptr, *D2 = nullptr;
+    // transposes (K-major operands of the weight gradients): H1^T, H2^T, D^T (D3^T, then D1^T),
+    // D2^T, F^T
+    drot::mlp::bf16 *H1T = nullptr, *H2T = nullptr, *DT = nullptr, *D2T = nullptr, *FT = nullptr;
     float *out = nullptr, *g = nullptr, *ebar = nullptr, *wsum = nullptr, *loss = nullptr;
     int seg_cap = 0;
     long long step = 0;
@@ -2098,8 +2103,9 @@ constexpr long long kOffW1 = 0, kOffB1 = kOffW1 + kW1, kOffW2 = kOffB1 + kB1, kO
 constexpr long long kOffW3 = kOffB2 + kB2, kOffB3 = kOffW3 + kW3, kOffW4 = kOffB3 + kB3, kOffB4 = kOffW4 + kW4;
 constexpr long long kParams = kOffB4 + kB4;
 static_assert(kParams == DROT_MLP_PARAMS, "parameter layout");
-// BF16 copies: W1, W2, W3 back to back
+// BF16 copies: W1, W2, W3 back to back; transposed copies: W2^T, W3^T
 constexpr long long kBfW1 = 0, kBfW2 = kW1, kBfW3 = kW1 + kW2, kBfCount = kW1 + kW2 + kW3;
+constexpr long long kBfT2 = 0, kBfT3 = kW2, kBfTCount = kW2 + kW3;
 
 #define MLP_CUDA(call)                                    \
     do {                                                  \
@@ -2108,14 +2114,21 @@ constexpr long long kBfW1 = 0, kBfW2 = kW1, kBfW3 = kW1 + kW2, kBfCount = kW1 + 
 
 drot_status mlp_reserve(drot_mlp *net, long long rows, int nseg) {
     if (rows > net->rows_cap) {
-        void *bufs[] = {net->H1, net->H2, net->H3, net->D, net->D2, net->out, net->g};
-        for (void *b : bufs)
-            if (b) cudaFree(b);
+        void **bufs[] = {(void **)&net->H1, (void **)&net->H2, (void **)&net->H3, (void **)&net->D,
+                         (void **)&net->D2, (void **)&net->out, (void **)&net->g, (void **)&net->H1T,
+                         (void **)&net->H2T, (void **)&net->DT, (void **)&net->D2T, (void **)&net->FT};
+        for (void **b : bufs) {
+            if (*b) cudaFree(*b);
+            *b = nullptr;
+        }
         const size_t hb = sizeof(M::bf16) * (size_t)rows * M::kWidth;
         if (cudaMalloc(&net->H1, hb) != cudaSuccess || cudaMalloc(&net->H2, hb) != cudaSuccess ||
             cudaMalloc(&net->H3, hb) != cudaSuccess || cudaMalloc(&net->D, hb) != cudaSuccess ||
             cudaMalloc(&net->D2, hb) != cudaSuccess || cudaMalloc(&net->out, sizeof(float) * rows) != cudaSuccess ||
-            cudaMalloc(&net->g, sizeof(float) * rows) != cudaSuccess) {
+            cudaMalloc(&net->g, sizeof(float) * rows) != cudaSuccess || cudaMalloc(&net->H1T, hb) != cudaSuccess ||
+            cudaMalloc(&net->H2T, hb) != cudaSuccess || cudaMalloc(&net->DT, hb) != cudaSuccess ||
+            cudaMalloc(&net->D2T, hb) != cudaSuccess ||
+            cudaMalloc(&net->FT, sizeof(M::bf16) * (size_t)rows * M::kIn) != cudaSuccess) {
             net->rows_cap = 0;
             return DROT_ERR_OOM;
         }
@@ -2132,27 +2145,58 @@ drot_status mlp_reserve(drot_mlp *net, long long rows, int nseg) {
     return DROT_OK;
 }
 
-template <bool TA, bool TB>
-cudaError_t mlp_gemm(cudaStream_t s, const M::bf16 *A, const M::bf16 *B, int Mr, int Nc, int K, int lda, int ldb,
-                     int epi, float *Cf, M::bf16 *Cb, int ldc, const float *bias, const M::bf16 *mask, int ksplit) {
-    const int tiles = (Mr / 32) * (Nc / 32);
-    dim3 grid((tiles + 3) / 4, 1, ksplit);
-    M::gemm_kernel<TA, TB><<<grid, 128, 0, s>>>(A, B, Mr, Nc, K, lda, ldb, epi, Cf, Cb, ldc, bias, mask);
+// C = A B^T on the tensor cores (A: Mr x K, B: Nc x K, both BF16 row-major).
+cudaError_t mlp_gemm(drot_mlp *net, const M::bf16 *A, int Mr, int K, int lda, const M::bf16 *B, int Nc, int ldb,
+                     int epi, float *Cf, M::bf16 *Cb, M::bf16 *CbT, int ldc, int ldt, const float *bias,
+                     const M::bf16 *mask) {
+    const drot::tc::EpiArgs E{epi, Cf, Cb, CbT, ldc, ldt, bias, mask, net->err};
+    if (Nc == M::kWidth) return drot::tc::gemm_tn<M::kWidth>(net->stream, A, Mr, K, lda, B, ldb, E);
+    if (Nc == M::kIn) return drot::tc::gemm_tn<M::kIn>(net->stream, A, Mr, K, lda, B, ldb, E);
+    return cudaErrorInvalidValue;
+}
+
+// Forward pass over `rows` feature rows (a multiple of 64): out[r].  train: also H1^T, H2^T.
+drot_status mlp_forward(drot_mlp *net, long long rows, const M::bf16 *F, bool train) {
+    cudaStream_t s = net->stream;
+    const int R = (int)rows;
+    const int W = M::kWidth;
+    MLP_CUDA(mlp_gemm(net, F, R, M::kIn, M::kIn, net->wb + kBfW1, W, M::kIn, M::kReluBiasBf16, nullptr, net->H1,
+                      train ? net->H1T : nullptr, W, R, net->w + kOffB1, nullptr));
+    MLP_CUDA(mlp_gemm(net, net->H1, R, W, W, net->wb + kBfW2, W, W, M::kReluBiasBf16, nullptr, net->H2,
+                      train ? net->H2T : nullptr, W, R, net->w + kOffB2, nullptr));
+    MLP_CUDA(mlp_gemm(net, net->H2, R, W, W, net->wb + kBfW3, W, W, M::kReluBiasBf16, nullptr, net->H3, nullptr, W,
+                      R, net->w + kOffB3, nullptr));
+    M::output_kernel<<<(R + 7) / 8, 256, 0, s>>>(net->H3, net->w + kOffW4, net->w + kOffB4, net->out, rows);
+    MLP_CUDA(cudaGetLastError());
+    return DROT_OK;
+}
+
+// BF16 copies of W1, W2, W3 and the transposes of W2, W3 from the FP32 parameters.
+cudaError_t mlp_refresh_bf16(drot_mlp *net) {
+    cudaStream_t s = net->stream;
+    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW1, net->wb + kBfW1, kW1);
+    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW2, net->wb + kBfW2, kW2);
+    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW3, net->wb + kBfW3, kW3);
     return cudaGetLastError();
 }
 
-// Forward pass over `rows` feature rows (a multiple of 64): out[r].
-drot_status mlp_forward(drot_mlp *net, long long rows, const M::bf16 *F) {
-    cudaStream_t s = net->stream;
-    const int R = (int)rows;
-    MLP_CUDA((mlp_gemm<false, true>(s, F, net->wb + kBfW1, R, M::kWidth, M::kIn, M::kIn, M::kIn, M::kReluBiasBf16,
-                                    nullptr, net->H1, M::kWidth, net->w + kOffB1, nullptr, 1)));
-    MLP_CUDA((mlp_gemm<false, true>(s, net->H1, net->wb + kBfW2, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
-                                    M::kReluBiasBf16, nullptr, net->H2, M::kWidth, net->w + kOffB2, nullptr, 1)));
-    MLP_CUDA((mlp_gemm<false, true>(s, net->H2, net->wb + kBfW3, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
-                                    M::kReluBiasBf16, nullptr, net->H3, M::kWidth, net->w + kOffB3, nullptr, 1)));
-    M::output_kernel<<<(R + 7) / 8, 256, 0, s>>>(net->H3, net->w + kOffW4, net->w + kOffB4, net->out, rows);
-    MLP_CUDA(cudaGetLastError());
+cudaError_t mlp_refresh_transposes(drot_mlp *net) {
+    const dim3 g(M::kWidth / 32, M::kWidth / 32);
+    M::transpose_bf16_kernel<<<g, 256, 0, net->stream>>>(net->wb + kBfW2, net->wbT + kBfT2, M::kWidth, M::kWidth);
+    M::transpose_bf16_kernel<<<g, 256, 0, net->stream>>>(net->wb + kBfW3, net->wbT + kBfT3, M::kWidth, M::kWidth);
+    return cudaGetLastError();
+}
+
+// DROT_ERR_TIMEOUT (and the flag cleared) if a tensor-core product gave up waiting.
+drot_status mlp_check_err(drot_mlp *net) {
+    int e = 0;
+    MLP_CUDA(cudaMemcpyAsync(&e, net->err, sizeof(int), cudaMemcpyDeviceToHost, net->stream));
+    MLP_CUDA(cudaStreamSynchronize(net->stream));
+    if (e) {
+        MLP_CUDA(cudaMemsetAsync(net->err, 0, sizeof(int), net->stream));
+        MLP_CUDA(cudaStreamSynchronize(net->stream));
+        return DROT_ERR_TIMEOUT;
+    }
     return DROT_OK;
 }
 
@@ -2179,6 +2223,8 @@ drot_status drot_mlp_create(drot_mlp **out, int device) {
     if (cudaMalloc(&net->w, pb) != cudaSuccess || cudaMalloc(&net->grad, pb) != cudaSuccess ||
         cudaMalloc(&net->m1, pb) != cudaSuccess || cudaMalloc(&net->m2, pb) != cudaSuccess ||
         cudaMalloc(&net->wb, sizeof(M::bf16) * kBfCount) != cudaSuccess ||
+        cudaMalloc(&net->wbT, sizeof(M::bf16) * kBfTCount) != cudaSuccess ||
+        cudaMalloc(&net->err, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&net->loss, sizeof(float)) != cudaSuccess) {
         drot_mlp_destroy(net);
         return DROT_ERR_OOM;
@@ -2187,6 +2233,8 @@ drot_status drot_mlp_create(drot_mlp **out, int device) {
     cudaMemsetAsync(net->m1, 0, pb, net->stream);
     cudaMemsetAsync(net->m2, 0, pb, net->stream);
     cudaMemsetAsync(net->wb, 0, sizeof(M::bf16) * kBfCount, net->stream);
+    cudaMemsetAsync(net->wbT, 0, sizeof(M::bf16) * kBfTCount, net->stream);
+    cudaMemsetAsync(net->err, 0, sizeof(int), net->stream);
     if (cudaStreamSynchronize(net->stream) != cudaSuccess) {
         drot_mlp_destroy(net);
         return DROT_ERR_CUDA;
@@ -2199,8 +2247,9 @@ drot_status drot_mlp_destroy(drot_mlp *net) {
     if (!net) return DROT_OK;
     cudaSetDevice(net->device);
     if (net->stream) cudaStreamSynchronize(net->stream);
-    void *bufs[] = {net->w, net->grad, net->m1, net->m2, net->wb, net->H1, net->H2, net->H3, net->D, net->D2,
-                    net->out, net->g, net->ebar, net->wsum, net->loss, net->feat, net->pred};
+    void *bufs[] = {net->w,   net->grad, net->m1,  net->m2,   net->wb,   net->wbT, net->err,  net->H1,
+                    net->H2,  net->H3,   net->D,   net->D2,   net->H1T,  net->H2T, net->DT,   net->D2T,
+                    net->FT,  net->out,  net->g,   net->ebar, net->wsum, net->loss, net->feat, net->pred};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (net->stream) cudaStreamDestroy(net->stream);
@@ -2216,10 +2265,8 @@ drot_status drot_mlp_set_params(drot_mlp *net, const float *params) {
     MLP_CUDA(cudaMemcpyAsync(net->w, params, pb, cudaMemcpyHostToDevice, s));
     MLP_CUDA(cudaMemsetAsync(net->m1, 0, pb, s));
     MLP_CUDA(cudaMemsetAsync(net->m2, 0, pb, s));
-    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW1, net->wb + kBfW1, kW1);
-    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW2, net->wb + kBfW2, kW2);
-    M::to_bf16_kernel<<<64, 256, 0, s>>>(net->w + kOffW3, net->wb + kBfW3, kW3);
-    MLP_CUDA(cudaGetLastError());
+    MLP_CUDA(mlp_refresh_bf16(net));
+    MLP_CUDA(mlp_refresh_transposes(net));
     net->step = 0;
     MLP_CUDA(cudaStreamSynchronize(s));
     return DROT_OK;
@@ -2248,11 +2295,10 @@ drot_status drot_mlp_forward(drot_mlp *net, int64_t rows, const void *feat, floa
     cudaSetDevice(net->device);
     drot_status st = mlp_reserve(net, rows, 1);
     if (st != DROT_OK) return st;
-    st = mlp_forward(net, rows, static_cast<const M::bf16 *>(feat));
+    st = mlp_forward(net, rows, static_cast<const M::bf16 *>(feat), false);
     if (st != DROT_OK) return st;
     MLP_CUDA(cudaMemcpyAsync(out, net->out, sizeof(float) * rows, cudaMemcpyDeviceToDevice, net->stream));
-    MLP_CUDA(cudaStreamSynchronize(net->stream));
-    return DROT_OK;
+    return mlp_check_err(net);
 }
 
 drot_status drot_mlp_train_step(drot_mlp *net, int64_t rows, const void *feat, const float *target,
@@ -2265,9 +2311,10 @@ drot_status drot_mlp_train_step(drot_mlp *net, int64_t rows, const void *feat, c
     if (st != DROT_OK) return st;
     cudaStream_t s = net->stream;
     const M::bf16 *F = static_cast<const M::bf16 *>(feat);
-    st = mlp_forward(net, rows, F);
+    st = mlp_forward(net, rows, F, true);
     if (st != DROT_OK) return st;
     const int R = (int)rows;
+    const int W = M::kWidth;
     MLP_CUDA(cudaMemsetAsync(net->grad, 0, sizeof(float) * kParams, s));
     MLP_CUDA(cudaMemsetAsync(net->ebar, 0, sizeof(float) * nseg, s));
     MLP_CUDA(cudaMemsetAsync(net->wsum, 0, sizeof(float) * nseg, s));
@@ -2275,27 +2322,29 @@ drot_status drot_mlp_train_step(drot_mlp *net, int64_t rows, const void *feat, c
     M::loss_pass1_kernel<<<256, 256, 0, s>>>(net->out, target, weight, seg, rows, net->ebar, net->wsum);
     M::loss_pass2_kernel<<<256, 256, 0, s>>>(net->out, target, weight, seg, rows, net->ebar, net->wsum,
                                              1.f / (float)nseg, net->g, net->loss);
-    // layer 4 and the gradient at the output of layer 3 (through its ReLU)
-    M::output_backward_kernel<<<R / 64, M::kWidth, 0, s>>>(net->g, net->H3, net->w + kOffW4, rows,
-                                                           net->grad + kOffW4, net->grad + kOffB4, net->D);
+    // layer 4 and the gradient at the output of layer 3 (through its ReLU): D3 and D3^T
+    M::output_backward_kernel<<<R / 64, W, 0, s>>>(net->g, net->H3, net->w + kOffW4, rows, net->grad + kOffW4,
+                                                   net->grad + kOffB4, net->D, net->DT);
+    // F^T for the weight gradient of layer 1
+    M::transpose_bf16_kernel<<<dim3(M::kIn / 32, R / 32), 256, 0, s>>>(F, net->FT, R, M::kIn);
     MLP_CUDA(cudaGetLastError());
-    const int ks = std::max(1, std::min(64, R / 256));
-    // layer 3: dW3 = D3^T H2, db3 = colsum D3, D2 = (D3 W3) o (H2 > 0)
-    MLP_CUDA((mlp_gemm<true, false>(s, net->D, net->H2, M::kWidth, M::kWidth, R, M::kWidth, M::kWidth, M::kAtomicF32,
-                                    net->grad + kOffW3, nullptr, M::kWidth, nullptr, nullptr, ks)));
-    M::column_sum_kernel<<<R / 64, M::kWidth, 0, s>>>(net->D, rows, net->grad + kOffB3);
-    MLP_CUDA((mlp_gemm<false, false>(s, net->D, net->wb + kBfW3, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
-                                     M::kMaskBf16, nullptr, net->D2, M::kWidth, nullptr, net->H2, 1)));
-    // layer 2: dW2 = D2^T H1, db2, D1 = (D2 W2) o (H1 > 0)  (D1 reuses D)
-    MLP_CUDA((mlp_gemm<true, false>(s, net->D2, net->H1, M::kWidth, M::kWidth, R, M::kWidth, M::kWidth,
-                                    M::kAtomicF32, net->grad + kOffW2, nullptr, M::kWidth, nullptr, nullptr, ks)));
-    M::column_sum_kernel<<<R / 64, M::kWidth, 0, s>>>(net->D2, rows, net->grad + kOffB2);
-    MLP_CUDA((mlp_gemm<false, false>(s, net->D2, net->wb + kBfW2, R, M::kWidth, M::kWidth, M::kWidth, M::kWidth,
-                                     M::kMaskBf16, nullptr, net->D, M::kWidth, nullptr, net->H1, 1)));
-    // layer 1: dW1 = D1^T F, db1
-    MLP_CUDA((mlp_gemm<true, false>(s, net->D, F, M::kWidth, M::kIn, R, M::kWidth, M::kIn, M::kAtomicF32,
-                                    net->grad + kOffW1, nullptr, M::kIn, nullptr, nullptr, ks)));
-    M::column_sum_kernel<<<R / 64, M::kWidth, 0, s>>>(net->D, rows, net->grad + kOffB1);
+    // layer 3: dW3 = D3^T H2 (K = rows, split over the grid), db3 = colsum D3,
+    // D2 = (D3 W3) o (H2 > 0) = D3 (W3^T)^T o mask, with D2^T
+    MLP_CUDA(mlp_gemm(net, net->DT, W, R, R, net->H2T, W, R, M::kAtomicF32, net->grad + kOffW3, nullptr, nullptr,
+                      W, 0, nullptr, nullptr));
+    M::column_sum_kernel<<<R / 64, W, 0, s>>>(net->D, rows, net->grad + kOffB3);
+    MLP_CUDA(mlp_gemm(net, net->D, R, W, W, net->wbT + kBfT3, W, W, M::kMaskBf16, nullptr, net->D2, net->D2T, W, R,
+                      nullptr, net->H2));
+    // layer 2: dW2 = D2^T H1, db2, D1 = (D2 W2) o (H1 > 0) with D1^T (D1 reuses D, D1^T reuses D^T)
+    MLP_CUDA(mlp_gemm(net, net->D2T, W, R, R, net->H1T, W, R, M::kAtomicF32, net->grad + kOffW2, nullptr, nullptr,
+                      W, 0, nullptr, nullptr));
+    M::column_sum_kernel<<<R / 64, W, 0, s>>>(net->D2, rows, net->grad + kOffB2);
+    MLP_CUDA(mlp_gemm(net, net->D2, R, W, W, net->wbT + kBfT2, W, W, M::kMaskBf16, nullptr, net->D, net->DT, W, R,
+                      nullptr, net->H1));
+    // layer 1: dW1 = D1^T F (N = feature width), db1
+    MLP_CUDA(mlp_gemm(net, net->DT, W, R, R, net->FT, M::kIn, R, M::kAtomicF32, net->grad + kOffW1, nullptr,
+                      nullptr, M::kIn, 0, nullptr, nullptr));
+    M::column_sum_kernel<<<R / 64, W, 0, s>>>(net->D, rows, net->grad + kOffB1);
     MLP_CUDA(cudaGetLastError());
     if (update) {
         net->step += 1;
@@ -2308,11 +2357,11 @@ drot_status drot_mlp_train_step(drot_mlp *net, int64_t rows, const void *feat, c
             M::adam_kernel<<<64, 256, 0, s>>>(net->w + g.off, net->grad + g.off, net->m1 + g.off, net->m2 + g.off,
                                               g.bf >= 0 ? net->wb + g.bf : nullptr, g.cnt, lr, b1, b2, 1e-8f, c1, c2);
         MLP_CUDA(cudaGetLastError());
+        MLP_CUDA(mlp_refresh_transposes(net));
     }
     if (loss) MLP_CUDA(cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     if (grad) MLP_CUDA(cudaMemcpyAsync(grad, net->grad, sizeof(float) * kParams, cudaMemcpyDeviceToHost, s));
-    MLP_CUDA(cudaStreamSynchronize(s));
-    return DROT_OK;
+    return mlp_check_err(net);
 }
 
 drot_status drot_mlp_warm_start(drot_mlp *net, int64_t m, int64_t n, const float *xs, const float *yt,
@@ -2340,7 +2389,7 @@ drot_status drot_mlp_warm_start(drot_mlp *net, int64_t m, int64_t n, const float
     MLP_CUDA(cudaMemsetAsync(net->feat, 0, sizeof(M::bf16) * rows * M::kIn, s));
     M::features_kernel<<<1, 256, 0, s>>>(xs, yt, p, q, m, n, net->feat, 0);
     MLP_CUDA(cudaGetLastError());
-    st = mlp_forward(net, rows, net->feat);
+    st = mlp_forward(net, rows, net->feat, false);
     if (st != DROT_OK) return st;
     // centred prediction in units of C, then the c-transforms (exact dual feasibility)
     M::centre_prediction_kernel<<<1, 1024, 0, s>>>(net->out, p, m, 1.0 / cost_scale, mu);
@@ -2351,8 +2400,7 @@ drot_status drot_mlp_warm_start(drot_mlp *net, int64_t m, int64_t n, const float
     drot::drot_init_plan_kernel<<<(int)std::min<long long>(1184, std::max<long long>(1, (work + 255) / 256)), 256, 0,
                                   s>>>(X, p, q, m, n, ld);
     MLP_CUDA(cudaGetLastError());
-    MLP_CUDA(cudaStreamSynchronize(s));
-    return DROT_OK;
+    return mlp_check_err(net);
 }
 
 }  // extern "C"

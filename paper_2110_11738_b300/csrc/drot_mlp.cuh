@@ -11,18 +11,17 @@
 //
 // Network: F (64) -> 256 -> 256 -> 256 -> 1, ReLU between layers.  Weights are
 // kept in FP32 (Adam state) with BF16 copies for the matrix products; activations
-// are stored in BF16; every product accumulates in FP32 (tensor-core MMA through
-// the wmma interface: these products are a few hundred MFLOP per training step,
-// far from any roofline, and not on the solver's hot path).
+// are stored in BF16; every product accumulates in FP32 in tensor memory (tcgen05.mma
+// with TMA-staged operands, drot_tc.cuh).
 #pragma once
 
 #include <cuda_bf16.h>
-#include <mma.h>
 
 #include <cstdint>
 #include <type_traits>
 
 #include "drot_kernels.cuh"
+#include "drot_tc.cuh"
 
 namespace drot {
 namespace mlp {
@@ -106,74 +105,25 @@ __global__ void __launch_bounds__(256) features_kernel(const float* xs, const fl
 
 // ---------------------------------------------------------------- matrix products
 //
-// C[M x N] = A[M x K] * B[K x N] with BF16 operands and FP32 accumulation.
-// TA: A is stored as its transpose (K x M, row-major); TB: B is stored as its
-// transpose (N x K, row-major).  M, N, K are multiples of 16 (32 for M, N).
-// Each warp owns a 32 x 32 block of C; gridDim.z splits K (split-K products add
-// into C with atomics).
-enum Epilogue : int {
-    kStoreF32 = 0,     // C = acc (FP32)
-    kReluBiasBf16 = 1, // H = bf16(max(acc + bias[n], 0))
-    kMaskBf16 = 2,     // D = bf16(acc * (mask[m, n] > 0))
-    kAtomicF32 = 3     // C += acc (FP32 atomics; split-K)
-};
+// Every product of the network (forward layers, the backward pass into the hidden layers,
+// the weight gradients) runs on the tcgen05 tensor cores through tc::gemm_tn (drot_tc.cuh):
+// C = A B^T with both operands K-major.  The layouts that makes necessary are kept next to
+// the natural ones: the training forward pass writes H1^T and H2^T beside H1 and H2, the
+// backward pass D^T beside D, the features are transposed once per step, and the BF16
+// weights W2, W3 have transposed copies (the backward pass multiplies by W, not W^T).
+using Epilogue = tc::Epilogue;
+constexpr int kStoreF32 = tc::kStoreF32, kReluBiasBf16 = tc::kReluBiasBf16, kMaskBf16 = tc::kMaskBf16,
+              kAtomicF32 = tc::kAtomicF32;
 
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) gemm_kernel(const bf16* A, const bf16* B, int M, int N, int K, int lda,
-                                                   int ldb, int epi, float* Cf, bf16* Cb, int ldc, const float* bias,
-                                                   const bf16* mask) {
-    using namespace nvcuda;
-    __shared__ float stage[4][32 * 32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_n = N / 32;
-    const int tile = blockIdx.x * 4 + warp;
-    if (tile >= (M / 32) * tiles_n) return;  // whole warp leaves together
-    const int tm = (tile / tiles_n) * 32, tn = (tile % tiles_n) * 32;
-    const int ksplit = gridDim.z;
-    const int kchunk = ((K / 16 + ksplit - 1) / ksplit) * 16;
-    const int k0 = blockIdx.z * kchunk, k1 = min(K, k0 + kchunk);
-
-    using LayA = typename std::conditional<TA, wmma::col_major, wmma::row_major>::type;
-    using LayB = typename std::conditional<TB, wmma::col_major, wmma::row_major>::type;
-    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) wmma::fill_fragment(acc[a][b], 0.f);
-    for (int k = k0; k < k1; k += 16) {
-        wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, LayA> fa[2];
-        wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, LayB> fb[2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const bf16* pa = TA ? A + (size_t)k * lda + (tm + 16 * a) : A + (size_t)(tm + 16 * a) * lda + k;
-            wmma::load_matrix_sync(fa[a], pa, lda);
-        }
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const bf16* pb = TB ? B + (size_t)(tn + 16 * b) * ldb + k : B + (size_t)k * ldb + (tn + 16 * b);
-            wmma::load_matrix_sync(fb[b], pb, ldb);
-        }
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) wmma::mma_sync(acc[a][b], fa[a], fb[b], acc[a][b]);
-    }
-    float* st = stage[warp];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-            wmma::store_matrix_sync(st + (16 * a) * 32 + 16 * b, acc[a][b], 32, wmma::mem_row_major);
-    __syncwarp();
-    for (int e = lane; e < 32 * 32; e += 32) {
-        const int r = tm + e / 32, c = tn + e % 32;
-        const float v = st[e];
-        const size_t o = (size_t)r * ldc + c;
-        if (epi == kStoreF32) Cf[o] = v;
-        else if (epi == kReluBiasBf16) Cb[o] = __float2bfloat16(fmaxf(v + bias[c], 0.f));
-        else if (epi == kMaskBf16) Cb[o] = __float2bfloat16(__bfloat162float(mask[o]) > 0.f ? v : 0.f);
-        else atomicAdd(Cf + o, v);
-    }
+// dst (cols x rows, pitch rows) = src^T (src: rows x cols, pitch cols), BF16; 32 x 32 tiles
+// through shared memory.  rows and cols are multiples of 32.
+__global__ void __launch_bounds__(256) transpose_bf16_kernel(const bf16* src, bf16* dst, int rows, int cols) {
+    __shared__ bf16 t[32][34];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int i = ty; i < 32; i += 8) t[i][tx] = src[(size_t)(r0 + i) * cols + c0 + tx];
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) dst[(size_t)(c0 + i) * rows + r0 + tx] = t[tx][i];
 }
 
 // ---------------------------------------------------------------- output layer, loss
@@ -224,9 +174,10 @@ __global__ void loss_pass2_kernel(const float* out, const float* y, const float*
 }
 
 // Output-layer backward: dW4[k] += sum_r g_r H3[r,k]; db4 += sum_r g_r;
-// D3[r,k] = bf16(g_r W4[k] (H3[r,k] > 0)).  One block per 64 rows, thread = k.
+// D3[r,k] = bf16(g_r W4[k] (H3[r,k] > 0)) and its transpose.  One block per 64 rows, thread = k.
 __global__ void __launch_bounds__(kWidth) output_backward_kernel(const float* g, const bf16* H3, const float* W4,
-                                                                  long long rows, float* dW4, float* db4, bf16* D3) {
+                                                                  long long rows, float* dW4, float* db4, bf16* D3,
+                                                                  bf16* D3T) {
     const int k = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * 64;
     float acc = 0.f, gs = 0.f;
@@ -234,7 +185,9 @@ __global__ void __launch_bounds__(kWidth) output_backward_kernel(const float* g,
         const float h = __bfloat162float(H3[r * kWidth + k]);
         acc += g[r] * h;
         gs += g[r];
-        D3[r * kWidth + k] = __float2bfloat16(h > 0.f ? g[r] * W4[k] : 0.f);
+        const bf16 d = __float2bfloat16(h > 0.f ? g[r] * W4[k] : 0.f);
+        D3[r * kWidth + k] = d;
+        D3T[(long long)k * rows + r] = d;  // D3^T (kWidth x rows) for the weight gradient of layer 3
     }
     atomicAdd(dW4 + k, acc);
     if (k == 0) atomicAdd(db4, gs);

@@ -26,11 +26,14 @@ def _bf16_features(rows, seed):
     return Fb, Fb.float().cpu().numpy().astype(np.float64)
 
 
-def test_forward_matches_reference():
+# 192 rows: one full and one half 128-row block per product; 65600 rows: 513 blocks (the
+# tensor cores of every SM busy), the last one ragged
+@pytest.mark.parametrize("rows", [192, 65600])
+def test_forward_matches_reference(rows):
     params = workloads.mlp_init_params(3)
     net = drot.Mlp(0, params)
-    Fb, F64 = _bf16_features(192, 1)
-    out = torch.zeros(192, dtype=torch.float32, device="cuda")
+    Fb, F64 = _bf16_features(rows, 1)
+    out = torch.zeros(rows, dtype=torch.float32, device="cuda")
     net.forward(Fb, out)
     ref, _ = ref_mlp.forward(params.astype(np.float64), F64)
     got = out.cpu().numpy()
@@ -39,11 +42,14 @@ def test_forward_matches_reference():
     net.close()
 
 
-def test_gradients_match_reference():
+# 256 rows: every weight-gradient product in one K range; 1088 rows: five K ranges per product
+# (the last one partly beyond the rows, read as zeros) added with atomics, and nine 128-row
+# blocks in the forward products, the last one ragged
+@pytest.mark.parametrize("rows", [256, 1088])
+def test_gradients_match_reference(rows):
     params = workloads.mlp_init_params(4)
     params[-257:-1] *= 8.0  # larger output weights: gradients well above rounding noise
     net = drot.Mlp(0, params)
-    rows = 256
     Fb, F64 = _bf16_features(rows, 2)
     rng = np.random.default_rng(3)
     y = rng.standard_normal(rows).astype(np.float32)
