@@ -263,6 +263,184 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tn_kernel(const __grid_const
     if (warp == 0) tmem_dealloc(tmem, (uint32_t)N);
 }
 
+// ------------------------------------------------------------------ persistent variant
+//
+// For products whose B is one weight matrix (K <= 256) shared by every row block: each CTA
+// loads B once and keeps it in shared memory, then walks row blocks blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Warp 0 (one lane) streams the blocks' A chunks through a ring
+// of kRing slots; warp 1 (one lane) issues the products into one of two TMEM accumulators and
+// commits each slot back to the producer once its products are done; warps 2-5 drain the
+// other accumulator (warp w reads TMEM lanes 32 (w mod 4) ..) while the next block's products
+// run, and hand it back.  Copies, products and epilogues of consecutive blocks overlap.
+constexpr int kRing = 5;               // A chunk slots of 16 KB
+constexpr int kResThreads = 192;       // producer warp, MMA warp, four epilogue warps
+
+__host__ __device__ constexpr int resident_smem_bytes(int N) {
+    return kMaxChunks * N * 128 + kRing * kBM * 128 + 1024 + 256;
+}
+
+// Bounded wait that also gives up as soon as another role of the block has (*abort).
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    for (uint32_t it = 0; it < kPollLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (it >= 64) __nanosleep(64);
+    }
+    *abort = 1;
+    return false;
+}
+
+template <int N>
+__device__ __forceinline__ void epilogue_row(const EpiArgs& E, const float (&v)[32], int r, int c0) {
+    if (E.kind == kAtomicF32 || E.kind == kStoreF32) {
+        float* dst = E.Cf + (size_t)r * E.ldc + c0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (E.kind == kAtomicF32) atomicAdd(dst + j, v[j]);
+            else dst[j] = v[j];
+        }
+        return;
+    }
+    __align__(16) bf16 o[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        float x;
+        if (E.kind == kReluBiasBf16) x = fmaxf(v[j] + E.bias[c0 + j], 0.f);
+        else x = __bfloat162float(E.mask[(size_t)r * E.ldc + c0 + j]) > 0.f ? v[j] : 0.f;
+        o[j] = __float2bfloat16(x);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(E.Cb + (size_t)r * E.ldc + c0);
+    const uint4* src = reinterpret_cast<const uint4*>(o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[j] = src[j];
+    if (E.CbT) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) E.CbT[(size_t)(c0 + j) * E.ldt + r] = o[j];
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kResThreads, 1) gemm_tn_resident_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                                          const __grid_constant__ CUtensorMap mapB,
+                                                                          int M, int kchunks, EpiArgs E) {
+    static_assert(N == 128 || N == 256, "two accumulators of N columns fit the 512 TMEM columns");
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    __shared__ volatile int s_consumed;  // A slots the MMA warp has taken (for the drain after an abort)
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint8_t* sB = base;                               // kchunks x N rows x 128 B, resident
+    uint8_t* sA = base + kMaxChunks * N * 128;        // kRing x 128 rows x 128 B
+    uint64_t* b_full = reinterpret_cast<uint64_t*>(sA + kRing * kBM * 128);
+    uint64_t* a_full = b_full + 1;
+    uint64_t* a_empty = a_full + kRing;
+    uint64_t* acc_full = a_empty + kRing;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;     // after an abort: every product issued has completed
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = (M + kBM - 1) / kBM;
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        s_consumed = 0;
+        mbar_init(b_full, 1);
+        for (int s = 0; s < kRing; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(&s_tmem, 2u * N);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer: B once, then the A chunks of every block through the ring
+        mbar_arrive_expect_tx(b_full, (uint32_t)kchunks * N * 128u);
+        for (int c = 0; c < kchunks; ++c) tma_load_2d(sB + c * N * 128, &mapB, c * kBK, 0, b_full);
+        int issued = 0;
+        for (int i = 0; i < my_tiles && !s_abort; ++i) {
+            const int m0 = ((int)blockIdx.x + i * (int)gridDim.x) * kBM;
+            for (int c = 0; c < kchunks; ++c, ++issued) {
+                const int slot = issued % kRing;
+                const uint32_t ph = (uint32_t)(issued / kRing) & 1u;
+                if (!wait_or_abort(&a_empty[slot], ph ^ 1u, &s_abort)) break;
+                mbar_arrive_expect_tx(&a_full[slot], kBM * 128u);
+                tma_load_2d(sA + slot * kBM * 128, &mapA, c * kBK, m0, &a_full[slot]);
+            }
+        }
+        if (s_abort) {
+            // copies still in flight land before the block leaves
+            wait_bounded(b_full, 0);
+            for (int j = s_consumed; j < issued; ++j) wait_bounded(&a_full[j % kRing], (uint32_t)(j / kRing) & 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        constexpr uint32_t idesc = mma_idesc(kBM, N);
+        bool ok = wait_or_abort(b_full, 0, &s_abort);
+        fence_after_sync();
+        int taken = 0;
+        for (int i = 0; ok && i < my_tiles; ++i) {
+            const int b = i & 1;
+            ok = wait_or_abort(&acc_empty[b], ((uint32_t)(i >> 1) & 1u) ^ 1u, &s_abort);
+            if (!ok) break;
+            fence_after_sync();
+            const uint32_t d = tmem + (uint32_t)(b * N);
+            for (int c = 0; c < kchunks; ++c, ++taken) {
+                const int slot = taken % kRing;
+                ok = wait_or_abort(&a_full[slot], (uint32_t)(taken / kRing) & 1u, &s_abort);
+                if (!ok) break;
+                s_consumed = taken + 1;
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(sA + slot * kBM * 128), b0 = smem_u32(sB + c * N * 128);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                    mma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                             (c > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&a_empty[slot]);  // the slot is free once these products are done
+            }
+            if (!ok) break;
+            mma_commit(&acc_full[b]);
+        }
+        if (!ok) {
+            // products already issued still write tensor memory: wait for all of them
+            mma_commit(drain);
+            wait_bounded(drain, 0);
+        }
+    } else if (warp >= 2) {
+        // ---- epilogue warps: TMEM lanes 32 g .. 32 g + 31 are rows 32 g .. of the block
+        const int g = warp & 3;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int b = i & 1;
+            if (!wait_or_abort(&acc_full[b], (uint32_t)(i >> 1) & 1u, &s_abort)) break;
+            fence_after_sync();
+            const int r = ((int)blockIdx.x + i * (int)gridDim.x) * kBM + g * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + (uint32_t)(b * N) + ((uint32_t)(g * 32) << 16) + (uint32_t)c0, v);
+                if (r < M) epilogue_row<N>(E, v, r, c0);
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0 && E.err) atomicExch(E.err, 1);
+    if (warp == 1) tmem_dealloc(tmem, 2u * N);
+}
+
 // ------------------------------------------------------------------ host side
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (the library does not link the
@@ -312,8 +490,23 @@ cudaError_t gemm_tn(cudaStream_t s, const bf16* A, int M, int K, int lda, const 
     const int kc = chunks < kMaxChunks ? chunks : kMaxChunks;
     const int splits = (chunks + kc - 1) / kc;
     if (splits > 1 && E.kind != kAtomicF32) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes(N));
+    cudaError_t e;
+    if constexpr (N == 256) {
+        if (splits == 1) {
+            // one weight matrix shared by every row block: the persistent kernel keeps it resident
+            int dev = 0, sms = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(gemm_tn_resident_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     resident_smem_bytes(N));
+            if (e != cudaSuccess) return e;
+            const int tiles = (M + kBM - 1) / kBM;
+            gemm_tn_resident_kernel<N><<<tiles < sms ? tiles : sms, kResThreads, resident_smem_bytes(N), s>>>(
+                ma, mb, M, kc, E);
+            return cudaGetLastError();
+        }
+    }
+    e = cudaFuncSetAttribute(gemm_tn_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(N));
     if (e != cudaSuccess) return e;
     gemm_tn_kernel<N><<<dim3((M + kBM - 1) / kBM, splits), kThreads, smem_bytes(N), s>>>(ma, mb, M, kc, E);
     return cudaGetLastError();

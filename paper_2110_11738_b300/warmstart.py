@@ -88,6 +88,44 @@ def build_training_set(problems: Sequence, mus: Sequence, net: drot.Mlp, device=
     return TrainingSet(feat=feat, target=target, weight=weight, seg=seg, row0=rows0, sizes=sizes)
 
 
+def labelled_training_set(make, count: int, net: drot.Mlp, solver: drot.Solver, tol: float, max_iter: int,
+                          device=0, chunk: int = 512):
+    """Label `count` problems with batched cold DROT solves and turn them into feature rows, one
+    chunk at a time: ``make(k)`` builds problem k (its cost preferably already on `device`), and
+    only one chunk's costs and plans are resident at once, so the set can hold tens of
+    thousands of problems.  Returns (TrainingSet, the label solves' result dicts)."""
+    import torch
+
+    feats, targets, weights, segs, sizes, results = [], [], [], [], [], []
+    for s in range(0, count, chunk):
+        part = [make(k) for k in range(s, min(count, s + chunk))]
+        dev = [_device_problem(pr, device) for pr in part]
+        results.extend(solver.solve_batched(dev, tol=tol, max_iter=max_iter, check=False))
+        rows = sum(pr.m for pr in part)
+        feat = torch.zeros((rows, drot.MLP_FEATURES), dtype=torch.bfloat16, device=device)
+        r0 = 0
+        for j, (pr, d) in enumerate(zip(part, dev)):
+            xs = torch.as_tensor(pr.x, dtype=torch.float32, device=device).contiguous()
+            yt = torch.as_tensor(pr.y, dtype=torch.float32, device=device).contiguous()
+            net.features(xs, yt, d["p"], d["q"], feat, r0)
+            targets.append((d["mu"] * pr.cost_scale).to(torch.float32))
+            weights.append(d["p"].to(torch.float32))
+            segs.append(torch.full((pr.m,), s + j, dtype=torch.int32, device=device))
+            sizes.append(pr.m)
+            r0 += pr.m
+        feats.append(feat)
+        del dev, part
+    total = sum(sizes)
+    rows = (total + ROW_PAD - 1) // ROW_PAD * ROW_PAD
+    pad = rows - total
+    feat = torch.cat(feats + [torch.zeros((pad, drot.MLP_FEATURES), dtype=torch.bfloat16, device=device)])
+    target = torch.cat(targets + [torch.zeros(pad, dtype=torch.float32, device=device)])
+    weight = torch.cat(weights + [torch.zeros(pad, dtype=torch.float32, device=device)])
+    seg = torch.cat(segs + [torch.full((pad,), -1, dtype=torch.int32, device=device)])
+    row0 = [int(x) for x in np.cumsum([0] + sizes[:-1])]
+    return TrainingSet(feat=feat, target=target, weight=weight, seg=seg, row0=row0, sizes=sizes), results
+
+
 def subset(ts: TrainingSet, idx: Sequence[int], device=0) -> TrainingSet:
     """The rows of problems `idx`, renumbered 0..len(idx)-1 and padded to a multiple of 64."""
     import torch
