@@ -17,7 +17,10 @@
 //     weight-gradient products of the backward pass.
 // A K range longer than 256 is split over gridDim.y, the partial products added with
 // atomics.  Rows of A beyond M and K beyond the operands' extent are read as zeros (TMA
-// out-of-bounds fill), so M and K need no padding to the block sizes.
+// out-of-bounds fill), so M and K need no padding to the block sizes.  Products of one
+// K range with N = 256 (every layer of the network against its weight matrix) use the
+// persistent variant below instead: B stays resident, A streams through a ring, and two
+// tensor-memory accumulators let one block's epilogue overlap the next block's products.
 //
 // Every wait is bounded: a CTA whose copies or products do not complete within the limit
 // records a fault in *err, waits (bounded again) for what it has issued, frees its tensor
@@ -269,11 +272,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tn_kernel(const __grid_const
 // loads B once and keeps it in shared memory, then walks row blocks blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Warp 0 (one lane) streams the blocks' A chunks through a ring
 // of kRing slots; warp 1 (one lane) issues the products into one of two TMEM accumulators and
-// commits each slot back to the producer once its products are done; warps 2-5 drain the
-// other accumulator (warp w reads TMEM lanes 32 (w mod 4) ..) while the next block's products
-// run, and hand it back.  Copies, products and epilogues of consecutive blocks overlap.
+// commits each slot back to the producer once its products are done; warps 2-9 drain the
+// other accumulator (warp w reads TMEM lanes 32 (w mod 4) .. and one half of the columns)
+// while the next block's products run, and hand it back.  Copies, products and epilogues of
+// consecutive blocks overlap.
 constexpr int kRing = 5;               // A chunk slots of 16 KB
-constexpr int kResThreads = 192;       // producer warp, MMA warp, four epilogue warps
+constexpr int kEpiWarps = 8;           // two per group of 32 TMEM lanes, one per column half
+constexpr int kResThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 
 __host__ __device__ constexpr int resident_smem_bytes(int N) {
     return kMaxChunks * N * 128 + kRing * kBM * 128 + 1024 + 256;
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(kResThreads, 1) gemm_tn_resident_kernel(const 
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+            mbar_init(&acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
         fence_mbar_init();
@@ -417,15 +422,17 @@ __global__ void __launch_bounds__(kResThreads, 1) gemm_tn_resident_kernel(const 
             wait_bounded(drain, 0);
         }
     } else if (warp >= 2) {
-        // ---- epilogue warps: TMEM lanes 32 g .. 32 g + 31 are rows 32 g .. of the block
+        // ---- epilogue warps: TMEM lanes 32 g .. 32 g + 31 are rows 32 g .. of the block;
+        // columns [h N / 2, (h + 1) N / 2)
         const int g = warp & 3;
+        const int h = (warp - 2) >> 2;
         for (int i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
             if (!wait_or_abort(&acc_full[b], (uint32_t)(i >> 1) & 1u, &s_abort)) break;
             fence_after_sync();
             const int r = ((int)blockIdx.x + i * (int)gridDim.x) * kBM + g * 32 + lane;
 #pragma unroll 1
-            for (int c0 = 0; c0 < N; c0 += 32) {
+            for (int c0 = h * (N / 2); c0 < (h + 1) * (N / 2); c0 += 32) {
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(b * N) + ((uint32_t)(g * 32) << 16) + (uint32_t)c0, v);
                 if (r < M) epilogue_row<N>(E, v, r, c0);
