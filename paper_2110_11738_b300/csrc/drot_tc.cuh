@@ -276,12 +276,30 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tn_kernel(const __grid_const
 // other accumulator (warp w reads TMEM lanes 32 (w mod 4) .. and one half of the columns)
 // while the next block's products run, and hand it back.  Copies, products and epilogues of
 // consecutive blocks overlap.
-constexpr int kRing = 5;               // A chunk slots of 16 KB
+constexpr int kRing = 4;               // A chunk slots of 16 KB
 constexpr int kEpiWarps = 8;           // two per group of 32 TMEM lanes, one per column half
 constexpr int kResThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+constexpr int kStageBytes = 2 * 32 * 32 * 2;       // per epilogue warp: a 32 x 32 BF16 tile and its transpose
 
 __host__ __device__ constexpr int resident_smem_bytes(int N) {
-    return kMaxChunks * N * 128 + kRing * kBM * 128 + 1024 + 256;
+    return kMaxChunks * N * 128 + kRing * kBM * 128 + kEpiWarps * kStageBytes + 1024 + 256;
+}
+
+// TMA tensor store of a 32 x 32 BF16 box from shared memory (bulk async-group of this thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of this thread's stores have been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's stores have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy writes to shared memory visible to the TMA (async proxy)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Bounded wait that also gives up as soon as another role of the block has (*abort).
@@ -327,7 +345,11 @@ __device__ __forceinline__ void epilogue_row(const EpiArgs& E, const float (&v)[
 template <int N>
 __global__ void __launch_bounds__(kResThreads, 1) gemm_tn_resident_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                           const __grid_constant__ CUtensorMap mapB,
-                                                                          int M, int kchunks, EpiArgs E) {
+                                                                          const __grid_constant__ CUtensorMap mapC,
+                                                                          const __grid_constant__ CUtensorMap mapCT,
+                                                                          int M, int kchunks, int tma_out, EpiArgs E) {
+    // tma_out: bit 0 = the BF16 result Cb is stored by TMA through mapC (32 x 32 boxes), bit 1 = its
+    // transpose CbT through mapCT; otherwise each thread stores its row directly
     static_assert(N == 128 || N == 256, "two accumulators of N columns fit the 512 TMEM columns");
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint32_t s_tmem;
@@ -337,7 +359,8 @@ __global__ void __launch_bounds__(kResThreads, 1) gemm_tn_resident_kernel(const 
     uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     uint8_t* sB = base;                               // kchunks x N rows x 128 B, resident
     uint8_t* sA = base + kMaxChunks * N * 128;        // kRing x 128 rows x 128 B
-    uint64_t* b_full = reinterpret_cast<uint64_t*>(sA + kRing * kBM * 128);
+    uint8_t* sStage = sA + kRing * kBM * 128;      // kEpiWarps x (32 x 32 tile, its transpose), BF16
+    uint64_t* b_full = reinterpret_cast<uint64_t*>(sStage + kEpiWarps * kStageBytes);
     uint64_t* a_full = b_full + 1;
     uint64_t* a_empty = a_full + kRing;
     uint64_t* acc_full = a_empty + kRing;
@@ -426,21 +449,67 @@ __global__ void __launch_bounds__(kResThreads, 1) gemm_tn_resident_kernel(const 
         // columns [h N / 2, (h + 1) N / 2)
         const int g = warp & 3;
         const int h = (warp - 2) >> 2;
+        bf16* stC = reinterpret_cast<bf16*>(sStage + (warp - 2) * kStageBytes);  // [32 rows][32 cols]
+        bf16* stT = stC + 32 * 32;                                                // [32 cols][32 rows]
         for (int i = 0; i < my_tiles; ++i) {
             const int b = i & 1;
             if (!wait_or_abort(&acc_full[b], (uint32_t)(i >> 1) & 1u, &s_abort)) break;
             fence_after_sync();
-            const int r = ((int)blockIdx.x + i * (int)gridDim.x) * kBM + g * 32 + lane;
+            const int rg = ((int)blockIdx.x + i * (int)gridDim.x) * kBM + g * 32;  // first row of the group
+            const int r = rg + lane;
 #pragma unroll 1
             for (int c0 = h * (N / 2); c0 < (h + 1) * (N / 2); c0 += 32) {
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(b * N) + ((uint32_t)(g * 32) << 16) + (uint32_t)c0, v);
-                if (r < M) epilogue_row<N>(E, v, r, c0);
+                if (!tma_out) {
+                    if (r < M) epilogue_row<N>(E, v, r, c0);
+                    continue;
+                }
+                // BF16 epilogue staged in shared memory and written by TMA stores (rows >= M are
+                // computed but clipped by the store)
+                __align__(16) bf16 o[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    float x;
+                    if (E.kind == kReluBiasBf16) x = fmaxf(v[j] + E.bias[c0 + j], 0.f);
+                    else x = (r < M && __bfloat162float(E.mask[(size_t)r * E.ldc + c0 + j]) > 0.f) ? v[j] : 0.f;
+                    o[j] = __float2bfloat16(x);
+                }
+                if (lane == 0) bulk_wait_read_all();  // the previous chunk's stores have read the stage
+                __syncwarp();
+                if (tma_out & 1) {
+                    uint4* dst = reinterpret_cast<uint4*>(stC + lane * 32);
+                    const uint4* src = reinterpret_cast<const uint4*>(o);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dst[j] = src[j];
+                } else if (r < M) {
+                    uint4* dst = reinterpret_cast<uint4*>(E.Cb + (size_t)r * E.ldc + c0);
+                    const uint4* src = reinterpret_cast<const uint4*>(o);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dst[j] = src[j];
+                }
+                if (tma_out & 2) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stT[j * 32 + lane] = o[j];
+                } else if (E.CbT && r < M) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) E.CbT[(size_t)(c0 + j) * E.ldt + r] = o[j];
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (rg < M) {  // a group wholly beyond the last row stores nothing
+                        if (tma_out & 1) tma_store_2d(&mapC, c0, rg, stC);
+                        if (tma_out & 2) tma_store_2d(&mapCT, rg, c0, stT);
+                    }
+                    bulk_commit();
+                }
             }
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
+        if (lane == 0) bulk_wait_all();  // every store of this warp has completed
     }
     fence_before_sync();
     __syncthreads();
@@ -473,16 +542,17 @@ inline EncodeTiledFn encode_tiled() {
 
 // Tensor map of a row-major rows x cols BF16 matrix with pitch ld (elements) read in boxes of
 // 64 columns x box_rows rows with the 128-byte swizzle; out-of-range elements read as 0.
-inline bool make_map(CUtensorMap* map, const bf16* ptr, long long rows, long long cols, long long ld, int box_rows) {
+inline bool make_map(CUtensorMap* map, const bf16* ptr, long long rows, long long cols, long long ld, int box_rows,
+                     int box_cols = kBK, bool swizzle = true) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15u) || (ld * 2) % 16 != 0 || rows < 1 || cols < 1) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     const cuuint32_t elem[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, elem,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // C = A B^T with A: M x K (pitch lda), B: N x K (pitch ldb), both BF16 row-major.  K ranges
@@ -507,9 +577,16 @@ cudaError_t gemm_tn(cudaStream_t s, const bf16* A, int M, int K, int lda, const 
             e = cudaFuncSetAttribute(gemm_tn_resident_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      resident_smem_bytes(N));
             if (e != cudaSuccess) return e;
+            // BF16 results (and their transposes) leave through TMA stores of 32 x 32 boxes
+            CUtensorMap mc{}, mct{};
+            int tma_out = 0;
+            if ((E.kind == kReluBiasBf16 || E.kind == kMaskBf16) && E.Cb) {
+                if (make_map(&mc, E.Cb, M, N, E.ldc, 32, 32, false)) tma_out |= 1;
+                if (E.CbT && make_map(&mct, E.CbT, N, M, E.ldt, 32, 32, false)) tma_out |= 2;
+            }
             const int tiles = (M + kBM - 1) / kBM;
             gemm_tn_resident_kernel<N><<<tiles < sms ? tiles : sms, kResThreads, resident_smem_bytes(N), s>>>(
-                ma, mb, M, kc, E);
+                ma, mb, mc, mct, M, kc, tma_out, E);
             return cudaGetLastError();
         }
     }
