@@ -153,6 +153,30 @@ def _weighted_corr(a, b, w):
     return (w * a * b).sum() / np.sqrt((w * a * a).sum() * (w * b * b).sum())
 
 
+def test_chunked_labelling_matches_the_whole_set_path():
+    """labelled_training_set (problems built on the device and labelled chunk by chunk, as the bench
+    does at twenty thousand problems) gives the same rows as labelling every problem first and
+    building the set afterwards: the costs are bit-identical, so features, weights and segments
+    match exactly; the labels are the same solves up to the order of the FP64 atomic sums, which
+    depends on how a batch is split over the CTAs."""
+    rule = drot.STOP_GAP | drot.STOP_RES_L1
+    sizes = [(96, 80), (130, 64), (64, 200), (101, 101), (77, 150)]
+    host = [workloads.make_problem("warm_1024", seed=300 + k, m=m, n=n) for k, (m, n) in enumerate(sizes)]
+    net = drot.Mlp(0, workloads.mlp_init_params(2))
+    with drot.Solver(device=0, stop_rule=rule) as solver:
+        mus, _ = warmstart.solve_labels(host, solver, tol=1e-4, max_iter=500_000, chunk=2)
+        ref = warmstart.build_training_set(host, mus, net)
+        ts, res = warmstart.labelled_training_set(
+            lambda k: workloads.make_problem("warm_1024", seed=300 + k, m=sizes[k][0], n=sizes[k][1], device="cuda"),
+            len(sizes), net, solver, tol=1e-4, max_iter=500_000, chunk=2)
+    assert len(res) == len(sizes) and all(r["status"] == drot.DROT_OK for r in res)
+    assert ts.sizes == ref.sizes and ts.row0 == ref.row0
+    assert ts.feat.shape == ref.feat.shape and torch.equal(ts.feat, ref.feat)
+    assert torch.equal(ts.seg, ref.seg) and torch.equal(ts.weight, ref.weight)
+    assert float((ts.target - ref.target).abs().max()) <= 1e-3 * float(ref.target.abs().max())
+    net.close()
+
+
 @pytest.fixture(scope="module")
 def trained_mixture_net():
     """A network trained on DROT's own duals of 128 small mixture-of-Gaussians problems (labels
