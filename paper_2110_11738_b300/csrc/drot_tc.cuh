@@ -275,7 +275,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tn_kernel(const __grid_const
 // commits each slot back to the producer once its products are done; warps 2-9 drain the
 // other accumulator (warp w reads TMEM lanes 32 (w mod 4) .. and one half of the columns)
 // while the next block's products run, and hand it back.  Copies, products and epilogues of
-// consecutive blocks overlap.
+// consecutive blocks overlap.  BF16 results leave through shared memory: each epilogue warp
+// stages a 32 x 32 tile (and, when asked, its transpose) and one lane writes it with a TMA
+// tensor store, so the stores are whole 64-byte rows instead of one thread's 16-byte pieces.
 constexpr int kRing = 4;               // A chunk slots of 16 KB
 constexpr int kEpiWarps = 8;           // two per group of 32 TMEM lanes, one per column half
 constexpr int kResThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
