@@ -142,7 +142,7 @@ typedef struct {
                                    partial sums are formed, hence the last bits of a run.  Also applies
                                    to drot_solve_batched; the FP64 solve always walks forwards */
     int batch_narrow;           /* drot_solve_batched: tiles with at most 256 valid columns go to a second
-                                   kernel that packs two or four rows into one warp iteration.  0 automatic
+                                   kernel that packs four or eight rows into one warp iteration.  0 automatic
                                    (while the active problems' narrow tiles hold at least 65536 rows: below
                                    that the extra launch costs more than packing saves), 1 always, -1 never */
 } drot_config;
