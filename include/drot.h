@@ -119,10 +119,15 @@ typedef struct {
                                    register-fed step and CUDA graphs (persistent is ignored) */
     int cluster;                /* small problems on one thread-block cluster (X and C held in shared
                                    memory for the whole solve, column and scalar totals exchanged in
-                                   distributed shared memory): 0 automatic (used when the problem fits
-                                   and none of step_variant, tile_k, grid_ctas, persistent,
-                                   deterministic, c_skip is set), 1 never, 2 required
-                                   (DROT_ERR_INVALID_ARG if the problem does not fit; c_skip off) */
+                                   distributed shared memory), mid-size ones grid-resident (one
+                                   cooperative launch of at most one CTA per SM, each holding its rows
+                                   of X and C in shared memory, two grid barriers per iteration):
+                                   0 automatic (the cluster where the problem fits, else grid-resident
+                                   where it fits and has at least 2e6 entries, when none of step_variant, tile_k, grid_ctas,
+                                   persistent, deterministic, c_skip, trace is set), 1 neither (the
+                                   streaming path), 2 cluster required, 3 grid-resident required
+                                   (2, 3: DROT_ERR_INVALID_ARG if the problem does not fit; FP32 only,
+                                   c_skip off) */
     double *trace;              /* optional device buffer of 2 * trace_len doubles, written during a solve:
                                    trace[2(k-1)] = <C, X_k> and trace[2(k-1)+1] = ||X_k 1 - p||_1 +
                                    ||X_k^T 1 - q||_1 for iterations k = 1 .. min(K, trace_len) (the

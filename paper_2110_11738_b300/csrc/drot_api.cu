@@ -25,6 +25,7 @@
 #include "drot_mlp.cuh"
 #include "drot_cluster.cuh"
 #include "drot_f64.cuh"
+#include "drot_grid.cuh"
 
 using drot::Scalars;
 
@@ -179,6 +180,36 @@ ClusterPlan cluster_plan(long long m, long long n) {
     return cp;
 }
 
+// Grid-resident solve: one CTA per SM (at most), rows and columns split evenly, X and C of a
+// CTA's rows in its shared memory; 0 CTAs if the rows do not fit.  Chosen automatically from
+// kGridMinEntries on: per iteration (µs, streaming graph / grid-resident, B300) 800^2 12.1 / 13.3,
+// 1000^2 12.5 / 14.2, 1200^2 14.3 / 16.0, 1400^2 15.3 / 16.2, 1500^2 19.8 / 16.3, 1600^2 20.1 / 17.7,
+// 1800^2 21.2 / 18.3: its two grid barriers and FP64 reduction chains cost more than the graph's
+// launch chain until the plan is large enough for the streaming step to leave L2-latency territory.
+constexpr long long kGridMinEntries = 2000000;
+struct GridPlan {
+    int G = 0, R = 0, Q = 0, npad = 0;
+    size_t smem = 0;
+};
+
+GridPlan grid_plan(long long m, long long n, int sms) {
+    GridPlan gp;
+    if (sms < 1 || m < 1 || n < 1) return gp;
+    const long long G0 = std::min<long long>(sms, m);
+    const int R = (int)((m + G0 - 1) / G0);
+    const int G = (int)((m + R - 1) / R);
+    const int Q = (int)((n + G - 1) / G);
+    const int npad = (int)((n + 3) / 4 * 4);
+    const size_t bytes = drot::grid_smem_bytes(R, Q, npad);
+    if (bytes > kClusterSmemMax) return gp;
+    gp.G = G;
+    gp.R = R;
+    gp.Q = Q;
+    gp.npad = npad;
+    gp.smem = bytes;
+    return gp;
+}
+
 template <int CS>
 cudaError_t launch_cluster(const ClusterPlan &cp, const drot::ClusterArgs &args, cudaStream_t s) {
     cudaLaunchConfig_t cfg{};
@@ -212,6 +243,9 @@ cudaError_t set_kernel_attributes() {
         e = cudaFuncSetAttribute(drot::drot_cluster_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(drot::drot_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kClusterSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(drot::drot_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kClusterSmemMax);
     return e;
 }
@@ -844,7 +878,60 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const void *C
         return fail(h, DROT_ERR_INVALID_ARG, "the cluster-resident solve is FP32 only");
     if (h->cfg.cluster == 2 && !use_cluster)
         return fail(h, DROT_ERR_INVALID_ARG, "a %lld x %lld problem does not fit on one cluster", m, n);
-    if (max_iter > 0 && use_cluster) {
+    // grid-resident: rows of X and C in the shared memory of one CTA per SM (mid-size problems)
+    const GridPlan gp = use_cluster ? GridPlan{} : grid_plan(m, n, h->num_sms);
+    const bool psi_fits = (size_t)P.slots * P.TW * sizeof(double) >= (size_t)n * sizeof(float);
+    const bool use_grid = !use_cluster && gp.G > 0 && psi_fits && !h->cfg.c_skip && !f64 &&
+                          (h->cfg.cluster == 3 ||
+                           (h->cfg.cluster == 0 && !explicit_stream && m * n >= kGridMinEntries));
+    if (h->cfg.cluster == 3 && !use_grid)
+        return fail(h, DROT_ERR_INVALID_ARG, "a %lld x %lld problem does not fit the grid-resident solve", m, n);
+    if (max_iter > 0 && use_grid) {
+        // one cooperative launch (one CTA per SM at most) runs up to `budget` iterations
+        drot::GridArgs ga{};
+        drot::ClusterArgs &ca = ga.P;
+        ca.C = C;
+        ca.X = X;
+        ca.p = p;
+        ca.q = q;
+        ca.g = h->g;
+        ca.h = h->h;
+        ca.a = h->a;
+        ca.b = h->b;
+        ca.sc = h->d_sc;
+        ca.m = m;
+        ca.n = n;
+        ca.ld = ld;
+        ca.rows_per_cta = gp.R;
+        ca.cols_per_cta = gp.Q;
+        ca.npad = gp.npad;
+        ca.inv_n = 1.0 / (double)n;
+        ca.inv_m = 1.0 / (double)m;
+        ca.inv_mn = 1.0 / (double)(m + n);
+        ca.budget = std::min<long long>(max_iter, 200000);
+        ga.v = h->v;
+        ga.psi_g = reinterpret_cast<float *>(h->colpart);
+        ga.totals = h->acc;
+        ga.bar = &h->gsync->count;
+        const long long max_launches = (max_iter + ca.budget - 1) / ca.budget + 2;
+        for (long long l = 0; l < max_launches; ++l) {
+            DROT_CUDA(h, cudaMemsetAsync(ga.v, 0, sizeof(double) * (size_t)n, h->stream));
+            DROT_CUDA(h, cudaMemsetAsync(ga.totals, 0, sizeof(double) * 2 * drot::kGridTotals, h->stream));
+            DROT_CUDA(h, cudaMemsetAsync(ga.bar, 0, sizeof(unsigned int), h->stream));
+            void *kargs[] = {&ga};
+            const cudaError_t e = cudaLaunchCooperativeKernel((const void *)drot::drot_grid_kernel, dim3(gp.G),
+                                                              dim3(drot::kGridThreads), kargs, gp.smem, h->stream);
+            if (e != cudaSuccess) return fail(h, DROT_ERR_CUDA, "grid-resident launch failed: %s", cudaGetErrorString(e));
+            h->prof.kernel_launches += 1;
+            DROT_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+            DROT_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (h->h_status->done != drot::kRunning || h->h_status->fault) {
+                done = h->h_status->fault ? drot::kFault : h->h_status->done;
+                break;
+            }
+        }
+        if (done == drot::kRunning) return fail(h, DROT_ERR_CUDA, "grid-resident iteration did not report completion");
+    } else if (max_iter > 0 && use_cluster) {
         // whole solve on one cluster; a launch runs up to `budget` iterations
         drot::ClusterArgs ca{};
         ca.C = C;
@@ -1016,8 +1103,8 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const void *C
     h->prof.grid_ctas = P.G;
     h->prof.col_tiles = P.T;
     h->prof.graph_iters = P.graph_iters;
-    h->prof.step_variant = f64 ? 5 : (use_cluster && max_iter > 0 ? 4 : P.variant);
-    h->prof.stages = use_cluster && max_iter > 0 ? cp.cs : P.S;
+    h->prof.step_variant = f64 ? 5 : (use_cluster && max_iter > 0 ? 4 : (use_grid && max_iter > 0 ? 6 : P.variant));
+    h->prof.stages = use_cluster && max_iter > 0 ? cp.cs : (use_grid && max_iter > 0 ? gp.G : P.S);
 
     drot_status out = DROT_OK;
     if (done == drot::kIterCap) out = DROT_NOT_CONVERGED;

@@ -95,6 +95,7 @@ SHAPES = [(1, 1), (3, 7), (31, 33), (130, 257), (257, 1031)]
 CONFIGS = {
     "automatic": {},  # cluster-resident where the problem fits
     "streaming": {"cluster": 1},
+    "grid_resident": {"cluster": 3},
     "registers_k1": {"step_variant": 1, "tile_k": 1},
     "tma_k2": {"step_variant": 2, "tile_k": 2},
     "async_k4": {"step_variant": 3, "tile_k": 4},

@@ -62,26 +62,31 @@ def test_every_golden_case_is_committed():
     assert {"gauss_384x512", "gauss_768x1024", "gauss_1536x2048"} <= names, names
 
 
-CASES = [(g, k) for g in GOLDEN for k in ((0, 4) if "1536x2048" in g else (0,))]
+# (tile_k, cluster): (0, 0) the automatic choice (grid-resident for 1536 x 2048, which has 3.1e6
+# entries), (0, 1) the autotuned streaming plan, (4, 0) the streaming step with the 512-column
+# tiles of the full-size workloads
+CASES = [(g, k, cl) for g in GOLDEN for k, cl in (((0, 0), (0, 1), (4, 0)) if "1536x2048" in g else ((0, 0),))]
 
 
-@pytest.mark.parametrize("path,tile_k", CASES, ids=[f"{os.path.basename(g)[9:-5]}-k{k}" for g, k in CASES])
-def test_full_rule_solve_matches_the_oracle(path, tile_k):
-    """tile_k 0: the autotuned plan; 4: the 512-column tiles of the full-size workloads."""
+@pytest.mark.parametrize("path,tile_k,cluster", CASES,
+                         ids=[f"{os.path.basename(g)[9:-5]}-k{k}-c{cl}" for g, k, cl in CASES])
+def test_full_rule_solve_matches_the_oracle(path, tile_k, cluster):
     gold = json.load(open(path))
     assert gold["status"] == oracle.STATUS_CONVERGED
     pr = workloads.make_problem(gold["workload"], seed=gold["seed"], m=gold["m"], n=gold["n"])
     assert _input_hash(pr.C, pr.p, pr.q) == gold["input_sha256"]
     C, p, q, X, mu, nu = _gpu_buffers(pr)
-    with drot.Solver(device=0, autotune=True, tile_k=tile_k) as s:
+    with drot.Solver(device=0, autotune=True, tile_k=tile_k, cluster=cluster) as s:
         out = s.solve(C, p, q, rho=pr.rho, tol=gold["tol"], max_iter=4_000_000, X=X, mu=mu, nu=nu)
         plan = s.profile()
     assert out["status"] == drot.DROT_OK, out
-    if pr.n >= 1536:
+    if pr.n >= 1536 and (tile_k or cluster == 1):
         # the streaming path on every CTA of the fused step, several column tiles
         assert plan["grid_ctas"] >= 2 * torch.cuda.get_device_properties(0).multi_processor_count
         assert plan["col_tiles"] >= 4 and plan["step_variant"] in (1, 2, 3)
         assert tile_k == 0 or plan["tile_k"] == tile_k
+    elif pr.n >= 1536:
+        assert plan["step_variant"] == 6  # grid-resident: rows of X and C in every SM's shared memory
     obj = gold["primal"]
     assert abs(out["primal_obj"] - obj) <= 1e-5 * abs(obj), (out["primal_obj"], obj)
     assert abs(out["dual_obj"] - gold["dual"]) <= 1e-5 * abs(obj) + 2 * gold["tol"]

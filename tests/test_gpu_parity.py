@@ -327,6 +327,26 @@ def test_cluster_solve_parity_plain_256():
     assert 0.5 * ref["iters"] <= out["iters"] <= 2.0 * ref["iters"]
 
 
+# grid-resident solve (cluster=3): the rows of X and C in the shared memory of one CTA per SM,
+# one CTA per row block (a single row for m <= 148), ragged last blocks, columns owned in blocks
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 7), (33, 129), (148, 200), (149, 301), (300, 2053), (1000, 1000),
+                                 (1536, 2048)])
+@pytest.mark.parametrize("k", [1, 4])
+def test_grid_resident_step_parity(m, n, k):
+    pr = workloads.make_problem("plain_8192x6144", seed=m * 13 + n, m=m, n=n)
+    with drot.Solver(device=0, cluster=3) as s:
+        _step_parity(s, pr, k, seed=m + n + 7 * k)
+        assert s.profile()["step_variant"] == 6  # grid-resident path taken
+
+
+def test_grid_resident_solve_parity_plain_256():
+    pr = workloads.make_problem("plain_256", seed=0)
+    with drot.Solver(device=0, cluster=3) as s:
+        out, ref = _solve_parity(s, pr)
+        assert s.profile()["step_variant"] == 6
+    assert 0.5 * ref["iters"] <= out["iters"] <= 2.0 * ref["iters"]
+
+
 def test_cluster_required_but_too_large():
     pr = workloads.make_problem("plain_256", seed=1, m=1200, n=1100)
     C, p, q, X, mu, nu = _gpu_inputs(pr)
