@@ -176,7 +176,9 @@ def drot_create(device: int = 0, stream: Optional[int] = None, stop_rule: int = 
     CUDA tensor of 2 * L entries that receives <C, X_k> and the l1 residual of iterations 1 .. L
     of every solve (the caller keeps it alive while the handle is used).  ``serpentine``: 1 or 0
     (default) alternates the direction of the fused-step passes so that each starts on what the
-    previous one left in L2; -1 runs every pass forwards.  ``batch_narrow`` (batched solves): 1
+    previous one left in L2; -1 runs every pass forwards.  ``cluster``: 0 chooses the on-chip
+    schemes automatically (one cluster for small problems, grid-resident from 2e6 entries where the
+    rows fit), 1 always streams, 2 requires the cluster, 3 the grid-resident solve.  ``batch_narrow`` (batched solves): 1
     always, -1 never, 0 (default) automatically sends tiles of at most 256 columns to the kernel
     that packs rows."""
     lib = load()

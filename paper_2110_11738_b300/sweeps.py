@@ -237,7 +237,8 @@ def main(argv=None) -> int:
     ar.add_argument("--sizes", type=int, nargs="+", default=[100, 200, 500, 1000, 2000, 5000, 10000, 20000])
     ar.add_argument("--runs", type=int, default=10)
     ar.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
-    ar.add_argument("--cluster", type=int, default=0, help="0 automatic, 1 never, 2 required")
+    ar.add_argument("--cluster", type=int, default=0,
+                    help="0 automatic, 1 streaming only, 2 cluster-resident required, 3 grid-resident required")
     for a in (a1, a3, ar):
         a.add_argument("--out", default=None)
         a.add_argument("--device", type=int, default=0)
