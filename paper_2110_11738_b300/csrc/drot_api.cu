@@ -973,7 +973,8 @@ drot_status solve_device(drot_handle *h, long long m, long long n, const void *C
         const long long budget = std::max(1LL, std::min<long long>(max_iter, std::llround(0.5 / t_iter)));
         const long long max_launches = (max_iter + budget - 1) / budget + 2;
         for (long long l = 0; l < max_launches; ++l) {
-            cudaError_t e = cudaSuccess;
+            cudaError_t e = cudaMemsetAsync(&h->gsync->count, 0, sizeof(unsigned int), h->stream);  // barrier counter
+            if (e != cudaSuccess) return fail(h, DROT_ERR_CUDA, "barrier reset failed: %s", cudaGetErrorString(e));
             switch (P.K) {
                 case 1: e = launch_persistent<1>(P.G, A, F, h->gsync, budget, h->stream); break;
                 case 2: e = launch_persistent<2>(P.G, A, F, h->gsync, budget, h->stream); break;

@@ -17,8 +17,8 @@
 //   4. grid barrier #2; every CTA reads the column-side totals, forms the dual objective, the
 //      gap, the norms and the stopping decision (identically), and copies psi into shared
 //      memory.
-// The barriers are one monotonic arrival counter (barrier t of a launch waits for (t + 1) G
-// arrivals); a CTA that waits longer than the spin limit, or sees another's fault, sets the
+// The barriers are one monotonic arrival counter (grid_barrier_counter: barrier t of a launch
+// waits for (t + 1) G arrivals); a CTA that waits longer than the spin limit, or sees another's fault, sets the
 // fault flag and the launch ends (DROT_ERR_TIMEOUT on the host).  Buffer reuse is ordered by
 // the barriers: v_j is reset by its only reader before barrier #2 and next added to after it;
 // psi is written between the barriers and read after #2, before the next #1; the totals of
@@ -84,36 +84,6 @@ __device__ inline GridSmem carve_grid_smem(unsigned char* base, int R, int Q, in
     S.hown = reinterpret_cast<double*>(take((size_t)Q * sizeof(double)));
     S.red = reinterpret_cast<double*>(take((kGridThreads / 32) * 8 * sizeof(double)));
     return S;
-}
-
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid barrier on a monotonic counter: returns false in every thread of the CTA if the wait
-// gave up (spin limit, or another CTA's fault).
-__device__ __forceinline__ bool grid_arrive_wait(unsigned int* bar, unsigned int target, Scalars* sc) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        int ok = 1;
-        unsigned long long spins = 0;
-        while (ld_acquire_u32(bar) < target) {
-            if (++spins > kBarrierSpins || ((spins & 255ull) == 0 && *(volatile int*)&sc->fault)) {
-                atomicExch(&sc->fault, 1);
-                ok = 0;
-                break;
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 __global__ void __launch_bounds__(kGridThreads, 1) drot_grid_kernel(GridArgs A) {
@@ -235,7 +205,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) drot_grid_kernel(GridArgs A) 
             atomicAdd(tot + tid, s);
         }
         target += (unsigned int)G;
-        if (!grid_arrive_wait(A.bar, target, sc)) break;  // #1: v and the row-side totals are complete
+        if (!grid_barrier_counter(A.bar, target, kBarrierSpins, sc)) break;  // #1: v and the row-side totals are complete
 
         // ---- 2. row-side totals and the new scalar c (every CTA identically)
         if (tid < 8) s_row[tid] = __ldcg(tot + tid);
@@ -272,7 +242,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) drot_grid_kernel(GridArgs A) 
         // the other parity's totals were last read before barrier #1 of this iteration
         if (blockIdx.x == 0 && tid >= 32 && tid < 32 + kGridTotals) tot_other[tid - 32] = 0.0;
         target += (unsigned int)G;
-        if (!grid_arrive_wait(A.bar, target, sc)) break;  // #2: psi and the column-side totals are complete
+        if (!grid_barrier_counter(A.bar, target, kBarrierSpins, sc)) break;  // #2: psi and the column-side totals are complete
 
         // ---- 4. totals, the stopping test (every CTA identically) and psi of the next pass
         if (tid == 0) {

@@ -1261,8 +1261,8 @@ __global__ void __launch_bounds__(kFinishThreads) drot_finish_kernel(FinishArgs 
 constexpr unsigned long long kBarrierSpins = 1ull << 24;
 
 struct GridSync {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int count;             // barrier arrivals of the current launch (cleared before each launch)
+    unsigned int pad;
     unsigned long long step_ns;     // time from each step's start to the end of its barrier (CTA 0)
     unsigned long long iters;       // iterations timed
     unsigned long long spin_limit;  // polls before a barrier wait gives up (0: kBarrierSpins)
@@ -1274,31 +1274,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Returns false (in every thread of the CTA) if the barrier gave up.
-__device__ __forceinline__ bool grid_barrier(GridSync* gs, Scalars* sc) {
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier on a monotonic arrival counter (cleared by the host before each launch):
+// barrier t of a launch waits until (t + 1) G CTAs have arrived, `target` holding (t + 1) G.
+// One atomic per CTA and a spin on one word (1.27 us per barrier on B300 with 148 CTAs, against
+// 2.39 us for a generation flip with back-off).  Returns false in every thread of the CTA if the
+// wait gave up: after `limit` polls, or on seeing another CTA's fault, it sets the fault flag.
+__device__ __forceinline__ bool grid_barrier_counter(unsigned int* count, unsigned int target,
+                                                     unsigned long long limit, Scalars* sc) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* gen = &gs->gen;
-        volatile int* fault = &sc->fault;
-        const unsigned int my_gen = *gen;
         __threadfence();
-        const unsigned int arrived = atomicAdd(&gs->count, 1u);
+        atomicAdd(count, 1u);
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&gs->count, 0u);
-            __threadfence();
-            atomicAdd(&gs->gen, 1u);
-        } else {
-            const unsigned long long limit = gs->spin_limit ? gs->spin_limit : kBarrierSpins;
-            unsigned long long spins = 0;
-            while (*gen == my_gen) {
-                if (++spins > limit || ((spins & 255ull) == 0 && *fault)) {
-                    atomicExch(&sc->fault, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        unsigned long long spins = 0;
+        while (ld_acquire_u32(count) < target) {
+            if (++spins > limit || ((spins & 255ull) == 0 && *(volatile int*)&sc->fault)) {
+                atomicExch(&sc->fault, 1);
+                ok = 0;
+                break;
             }
         }
         __threadfence();
@@ -1308,22 +1308,29 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, Scalars* sc) {
     return s_ok != 0;
 }
 
+// The persistent solve's barrier (GridSync::spin_limit polls, or kBarrierSpins).
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, Scalars* sc, unsigned int& target) {
+    target += gridDim.x;
+    return grid_barrier_counter(&gs->count, target, gs->spin_limit ? gs->spin_limit : kBarrierSpins, sc);
+}
+
 template <int K>
 __global__ void __launch_bounds__(kThreads, 2) drot_persistent_kernel(StepArgs A, FinishArgs F, GridSync* gs,
                                                                       long long budget) {
     __shared__ StepSmem<K> sm;
     Scalars* sc = F.sc;
+    unsigned int target = 0;  // arrivals the next barrier waits for (the counter is 0 at launch)
     for (long long it = 0; it < budget; ++it) {
         if (*(volatile int*)&sc->done != kRunning) break;  // uniform: read after a barrier
         const unsigned long long t0 = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
         step_pass<K, true, 0>(A, blockIdx.x, sm, A.serp != 0 && (it & 1) != 0);
-        if (!grid_barrier(gs, sc)) return;
+        if (!grid_barrier(gs, sc, target)) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             gs->step_ns += global_ns() - t0;
             gs->iters += 1;
         }
         finish_body<kThreads>(F, blockIdx.x, gridDim.x);
-        if (!grid_barrier(gs, sc)) return;
+        if (!grid_barrier(gs, sc, target)) return;
     }
 }
 
